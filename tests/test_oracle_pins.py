@@ -1,0 +1,268 @@
+"""Pins for the FP64 oracle against what mathematics and library routines fix.
+
+Nothing here compares the oracle with itself: each check is a closed form, an
+invariant, an exact special case, or a scipy/numpy routine. Together they cover every
+step: pyramid, propagation, warp, gradient, residual, window sums, solve and the
+coarse-to-fine driver (Sect. 2.4).
+"""
+import numpy as np
+import pytest
+from scipy import ndimage, signal
+
+from paper_1306_2461_gb300 import synth
+
+
+def valid(a, m):
+    return a[m:-m, m:-m]
+
+
+# ------------------------------------------------------------------ whole pipeline
+@pytest.mark.parametrize("H,W,L,r,n", [(64, 80, 3, 4, 3), (37, 53, 2, 5, 2), (256, 256, 2, 5, 4),
+                                       (9, 7, 4, 10, 2), (1, 1, 1, 1, 1)])
+def test_identical_images_give_exactly_zero_flow(oracle_mod, H, W, L, r, n):
+    # I1 == I2: at zero flow every sample is at an integer position, e = 0, so the
+    # right-hand side is H u = 0 and the solve returns exactly 0 at every level.
+    rng = np.random.default_rng(H * W)
+    I = rng.integers(0, 4096, (H, W)).astype(np.float64)
+    u, v = oracle_mod.flow(I, I, L, r, n)
+    assert np.all(u == 0.0) and np.all(v == 0.0)
+
+
+def test_integer_translation_is_a_fixed_point_reached_exactly(oracle_mod):
+    # For an integer shift bilinear sampling is exact, so the true shift is an exact
+    # fixed point of the iteration; the pyramid must converge onto it.
+    d = (3.0, -2.0)
+    I1, I2 = synth.translated_texture_pair(128, 160, d, seed=1)
+    L, r, n = 3, 4, 12
+    u, v = oracle_mod.flow(I1, I2, L, r, n)
+    m = (r + 2) * 2 ** (L - 1)
+    assert np.abs(valid(u, m) - d[0]).max() < 1e-6
+    assert np.abs(valid(v, m) - d[1]).max() < 1e-6
+
+
+def test_subpixel_translation_recovered(oracle_mod):
+    # Uniform (1.3, -0.7) px translation of a band-limited texture (frequencies
+    # <= 1/16 cycles/px), window radius 10 as in Sect. 2.4. The recovered translation
+    # (mean and median over valid pixels) is within 0.01 px. Per pixel, bilinear
+    # interpolation leaves a residual ~ t(1-t)/2 * laplacian(T) (t = 0.3), which the
+    # window turns into a bias of order 0.21 * 2/(2r+1) ~ 0.02 px; bound it at 0.05.
+    d = (1.3, -0.7)
+    I1, I2 = synth.translated_texture_pair(128, 128, d, seed=1)
+    L, r, n = 2, 10, 10
+    u, v = oracle_mod.flow(I1, I2, L, r, n)
+    m = (r + 2) * 2 ** (L - 1)
+    eu, ev = valid(u, m) - d[0], valid(v, m) - d[1]
+    assert abs(eu.mean()) < 0.01 and abs(ev.mean()) < 0.01
+    assert np.median(np.maximum(np.abs(eu), np.abs(ev))) < 0.01
+    assert max(np.abs(eu).max(), np.abs(ev).max()) < 0.05
+
+
+def test_swapping_images_negates_flow(oracle_mod):
+    d = (1.3, -0.7)
+    I1, I2 = synth.translated_texture_pair(128, 128, d, seed=3)
+    L, r, n = 2, 10, 10
+    u, v = oracle_mod.flow(I1, I2, L, r, n)
+    us, vs = oracle_mod.flow(I2, I1, L, r, n)
+    m = (r + 2) * 2 ** (L - 1)
+    su, sv = valid(u + us, m), valid(v + vs, m)
+    assert abs(su.mean()) < 0.02 and abs(sv.mean()) < 0.02
+    assert np.median(np.abs(su)) < 0.02 and np.median(np.abs(sv)) < 0.02
+    assert abs(valid(u, m).mean() - d[0]) < 0.01    # and it is the right translation
+
+
+def test_particle_pair_recovers_ground_truth(oracle_mod):
+    # Not a parity pin: the method on the 256^2 particle workload lands near the
+    # analytic displacement (guards against a gross error the pins above might miss).
+    p = synth.make_c1()
+    u, v = oracle_mod.flow(p.I1, p.I2, 2, 5, 4)
+    m = (5 + 2) * 2
+    epe = np.sqrt((u - p.u_gt) ** 2 + (v - p.v_gt) ** 2)
+    assert np.sqrt((valid(epe, m) ** 2).mean()) < 0.15
+    assert abs(valid(u, m).mean() - 1.3) < 0.02 and abs(valid(v, m).mean() + 0.7) < 0.02
+
+
+def test_thread_count_does_not_change_result(oracle_mod):
+    p = synth.make_c1(96, 112, seed=5)
+    n0 = oracle_mod.threads()
+    try:
+        oracle_mod.set_threads(1)
+        a = oracle_mod.flow(p.I1, p.I2, 2, 4, 3)
+        oracle_mod.set_threads(max(2, n0))
+        b = oracle_mod.flow(p.I1, p.I2, 2, 4, 3)
+    finally:
+        oracle_mod.set_threads(n0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ------------------------------------------------------------------------ steps
+@pytest.mark.parametrize("H,W,r", [(7, 9, 2), (3, 3, 5), (1, 1, 3), (16, 5, 4), (31, 33, 10)])
+def test_window_sum_matches_convolution(oracle_mod, H, W, r):
+    # Integer-valued inputs: both sums are exact, so equality is exact.
+    rng = np.random.default_rng(H + 100 * W + r)
+    c = rng.integers(-1000, 1000, (H, W)).astype(np.float64)
+    ref = signal.convolve2d(c, np.ones((2 * r + 1, 2 * r + 1)), mode="same", boundary="fill")
+    assert np.array_equal(oracle_mod.window_sum(c, r), ref)
+
+
+def test_solve_matches_library_on_spd(oracle_mod):
+    rng = np.random.default_rng(7)
+    n = 2000
+    A = rng.standard_normal((n, 2, 2))
+    M = A @ A.transpose(0, 2, 1) + 0.1 * np.eye(2)
+    b = rng.standard_normal((n, 2))
+    xu, xv, q, ok = oracle_mod.solve(M[:, 0, 0], M[:, 0, 1], M[:, 1, 1], b[:, 0], b[:, 1])
+    ref = np.linalg.solve(M, b[..., None])[..., 0]
+    tr = M[:, 0, 0] + M[:, 1, 1]
+    det = np.linalg.det(M)
+    good = det > 1e-6 * tr * tr
+    assert good.mean() > 0.9
+    np.testing.assert_allclose(xu[good], ref[good, 0], rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(xv[good], ref[good, 1], rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(q, det / tr ** 2, rtol=1e-9, atol=1e-12)
+    assert np.array_equal(ok, good)
+
+
+def test_solve_singular_guard_keeps_fallback(oracle_mod):
+    # rank-1 (aperture problem), zero matrix, negative trace: no solution; the
+    # fallback (the current estimate) is returned unchanged.
+    Sa = np.array([4.0, 0.0, -1.0, 1.0])
+    Sb = np.array([2.0, 0.0, 0.0, 0.0])
+    Sc = np.array([1.0, 0.0, -1.0, 1e-9])
+    Sd = np.ones(4)
+    Se = np.ones(4)
+    fu = np.array([0.5, -1.5, 2.0, 3.0])
+    fv = np.array([-0.25, 0.75, 1.0, 4.0])
+    xu, xv, q, ok = oracle_mod.solve(Sa, Sb, Sc, Sd, Se, fu, fv)
+    assert not ok.any()
+    assert np.array_equal(xu, fu) and np.array_equal(xv, fv)
+    assert q[0] == 0.0 and q[1] == -1.0 and q[2] == -1.0
+
+
+def test_aperture_problem_ramp_keeps_estimate(oracle_mod):
+    # I = a x + b y: every gradient is (a, b), the window matrix has rank 1 and the
+    # guard keeps the current estimate exactly (exact binary fractions, so det == 0).
+    H, W = 24, 20
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    P2 = 0.5 * x + 0.25 * y
+    P1 = P2 + 1.0
+    u0 = np.zeros((H, W))
+    u1, v1, q = oracle_mod.lk_iteration(P1, P2, u0, u0, 3)
+    inner = (slice(4, -4), slice(4, -4))   # windows that see no clamped border gradient
+    assert np.all(u1[inner] == 0.0) and np.all(v1[inner] == 0.0)
+    assert np.all(q[4:-4, 4:-4] == 0.0)
+
+
+@pytest.mark.parametrize("H,W", [(16, 16), (17, 23), (1, 9), (2, 2), (5, 1)])
+def test_pyramid_matches_separable_library_filter(oracle_mod, H, W):
+    rng = np.random.default_rng(H * 31 + W)
+    img = rng.uniform(0, 255, (H, W))
+    k = np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16.0
+    ref = ndimage.correlate1d(ndimage.correlate1d(img, k, axis=0, mode="nearest"), k, axis=1,
+                              mode="nearest")[::2, ::2]
+    out = oracle_mod.pyr_down(img)
+    assert out.shape == ((H + 1) // 2, (W + 1) // 2)
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-12)
+
+
+def test_pyramid_constant_and_linear(oracle_mod):
+    H, W = 20, 26
+    c = oracle_mod.pyr_down(np.full((H, W), 37.25))
+    assert np.all(c == 37.25)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    ramp = 5.0 + 0.75 * x - 1.5 * y
+    out = oracle_mod.pyr_down(ramp)
+    i, j = np.mgrid[0:out.shape[0], 0:out.shape[1]].astype(np.float64)
+    expect = 5.0 + 0.75 * 2 * j - 1.5 * 2 * i
+    # the binomial filter preserves linear functions; clamp-to-edge breaks that only
+    # within 2 source pixels (1 output pixel) of the border
+    np.testing.assert_allclose(out[1:-1, 1:-1], expect[1:-1, 1:-1], atol=1e-12)
+
+
+def test_upsample_constant_linear_and_library(oracle_mod):
+    Hc, Wc, H, W = 9, 12, 17, 24
+    assert np.all(oracle_mod.upsample_flow(np.full((Hc, Wc), -1.25), H, W) == -2.5)
+    i, j = np.mgrid[0:Hc, 0:Wc].astype(np.float64)
+    lin = 0.5 + 0.25 * j - 0.125 * i
+    up = oracle_mod.upsample_flow(lin, H, W)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    inside = (x / 2 <= Wc - 1) & (y / 2 <= Hc - 1)
+    np.testing.assert_allclose(up[inside], (2 * (0.5 + 0.25 * x / 2 - 0.125 * y / 2))[inside], atol=1e-12)
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal((Hc, Wc))
+    ref = 2 * ndimage.map_coordinates(f, [np.minimum(y / 2, Hc - 1), np.minimum(x / 2, Wc - 1)],
+                                      order=1, mode="nearest")
+    np.testing.assert_allclose(oracle_mod.upsample_flow(f, H, W), ref, atol=1e-12)
+
+
+def test_warp_matches_library_interpolation(oracle_mod):
+    H, W = 21, 30
+    rng = np.random.default_rng(2)
+    I2 = rng.uniform(0, 100, (H, W))
+    u = rng.uniform(-4, 4, (H, W))
+    v = rng.uniform(-4, 4, (H, W))
+    Iw, gx, gy = oracle_mod.warp_grad(I2, u, v)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    ref = ndimage.map_coordinates(I2, [np.clip(y + v, 0, H - 1), np.clip(x + u, 0, W - 1)],
+                                  order=1, mode="nearest")
+    np.testing.assert_allclose(Iw, ref, atol=1e-10)
+
+
+def test_gradient_exact_on_quadratic_with_integer_flow(oracle_mod):
+    # Integer displacements: samples are exact, and the central difference of a
+    # quadratic is its exact derivative at the displaced position.
+    H, W = 30, 34
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    a, b, c, d, e = 0.03, -0.02, 0.05, 1.5, -0.75
+    I2 = a * x * x + b * y * y + c * x * y + d * x + e * y
+    rng = np.random.default_rng(3)
+    u = rng.integers(-3, 4, (H, W)).astype(np.float64)
+    v = rng.integers(-3, 4, (H, W)).astype(np.float64)
+    Iw, gx, gy = oracle_mod.warp_grad(I2, u, v)
+    px, py = x + u, y + v
+    ok = (px >= 1) & (px <= W - 2) & (py >= 1) & (py <= H - 2)
+    assert ok.mean() > 0.7
+    np.testing.assert_allclose(Iw[ok], (a * px * px + b * py * py + c * px * py + d * px + e * py)[ok],
+                               atol=1e-9)
+    np.testing.assert_allclose(gx[ok], (2 * a * px + c * py + d)[ok], atol=1e-9)
+    np.testing.assert_allclose(gy[ok], (2 * b * py + c * px + e)[ok], atol=1e-9)
+    # at the image border the outside sample clamps to the edge: one-sided, still /2
+    edge = (px == 0) & (py >= 1) & (py <= H - 2)
+    if edge.any():
+        f = lambda X, Y: a * X * X + b * Y * Y + c * X * Y + d * X + e * Y
+        np.testing.assert_allclose(gx[edge], ((f(px + 1, py) - f(px, py)) / 2)[edge], atol=1e-9)
+
+
+def test_one_iteration_with_integer_flow_matches_library_solve(oracle_mod):
+    # With an integer flow field every sample is an exact array lookup, so one
+    # Gauss-Newton step reduces to: products of exact lookups, box sums
+    # (scipy convolution) and per-pixel 2x2 solves (numpy.linalg.solve).
+    H, W, r = 26, 31, 3
+    rng = np.random.default_rng(11)
+    P1 = rng.uniform(0, 200, (H, W))
+    P2 = rng.uniform(0, 200, (H, W))
+    u = rng.integers(-2, 3, (H, W)).astype(np.float64)
+    v = rng.integers(-2, 3, (H, W)).astype(np.float64)
+    y, x = np.mgrid[0:H, 0:W]
+    X = np.clip(x + u.astype(int), 0, W - 1)
+    Y = np.clip(y + v.astype(int), 0, H - 1)
+    Iw = P2[Y, X]
+    gx = (P2[Y, np.clip(x + u.astype(int) + 1, 0, W - 1)] - P2[Y, np.clip(x + u.astype(int) - 1, 0, W - 1)]) / 2
+    gy = (P2[np.clip(y + v.astype(int) + 1, 0, H - 1), X] - P2[np.clip(y + v.astype(int) - 1, 0, H - 1), X]) / 2
+    et = P1 - Iw + gx * u + gy * v
+    box = np.ones((2 * r + 1, 2 * r + 1))
+    S = [signal.convolve2d(c, box, mode="same") for c in (gx * gx, gx * gy, gy * gy, gx * et, gy * et)]
+    M = np.stack([np.stack([S[0], S[1]], -1), np.stack([S[1], S[2]], -1)], -2)
+    ref = np.linalg.solve(M, np.stack([S[3], S[4]], -1)[..., None])[..., 0]
+    u1, v1, q = oracle_mod.lk_iteration(P1, P2, u, v, r)
+    assert (q > 1e-6).all()
+    np.testing.assert_allclose(u1, ref[..., 0], rtol=1e-7, atol=1e-7)
+    np.testing.assert_allclose(v1, ref[..., 1], rtol=1e-7, atol=1e-7)
+
+
+def test_level_sizes_halve_with_ceiling(oracle_mod):
+    assert oracle_mod.level_size(1024, 1024, 2) == (256, 256)
+    assert oracle_mod.level_size(1088, 2048, 3) == (136, 256)
+    assert oracle_mod.level_size(383, 1791, 2) == (96, 448)
+    assert oracle_mod.level_size(1, 1, 5) == (1, 1)
+    I = np.zeros((383, 1791))
+    assert [p.shape for p in oracle_mod.pyramid(I, 3)] == [(383, 1791), (192, 896), (96, 448)]
