@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark: vector fields/s and latency of the dense pyramidal Lucas-Kanade flow at
+1024^2 (12-bit particle images, Lamb-Oseen vortex + shear layer, 3 levels, window radius
+4, 5 iterations per level), FP16-storage batched form vs plain FP32 single pair, with
+the fraction of the HBM roofline.
+
+One step = the whole method (pyramids + all iterations on all levels) for a batch of
+pairs, one persistent launch through of_compute_batch; inputs are resident in HBM when
+the timed region starts and the step's working set is far above the L2 size.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+
+Multi-GPU (torchrun, one process per GPU): fields are independent, so each rank runs
+its own replica of the batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vector fields/s & p99 latency at 1024², FP16-storage vs FP32, % HBM roofline"
+UNIT = "fields/s"
+H = W = 1024
+LEVELS, RADIUS, ITERS, BITS = 3, 4, 5, 12
+WORKLOAD = "pair1024_u16_vortex_shear"
+DISTINCT = 8          # distinct seeded pairs; the batch cycles through them
+
+
+def level_sizes(H, W, L):
+    out = []
+    for _ in range(L):
+        out.append((H, W))
+        H, W = (H + 1) // 2, (W + 1) // 2
+    return out
+
+
+def algorithmic_bytes(H, W, L, n, s, raw):
+    """Minimum HBM bytes of one field for this dataflow (each byte read or written once):
+    pyramids: read raw (raw B/px) once, write every level at s B/px, read levels 1..L-2
+    once to build the next; iterations: read I1 and I2 (s each) and the current (u, v)
+    (8 B), write the new (u, v) (8 B) per pixel, except that the first iteration on the
+    coarsest level reads no flow and the first on a finer level reads the coarse one."""
+    lv = level_sizes(H, W, L)
+    N = [h * w for h, w in lv]
+    pyr = 2 * (raw * N[0] + s * sum(N) + s * sum(N[1:L - 1]))
+    it = 0
+    for l in range(L):
+        for k in range(n):
+            rd_flow = 0 if (k == 0 and l == L - 1) else (8 * N[l + 1] if k == 0 else 8 * N[l])
+            it += 2 * s * N[l] + rd_flow + 8 * N[l]
+    return pyr + it, pyr, it
+
+
+def pixel_iterations(H, W, L, n):
+    return n * sum(h * w for h, w in level_sizes(H, W, L))
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1306_2461_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this
+    exact kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "batch_kernel_pair1024_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 2 and not line.startswith("#"):
+            kv[parts[0]] = parts[1]
+    if kv.get("kernel_source_sha1") != kernel_hash:
+        return None
+    try:
+        return float(kv["bytes_per_launch_full_batch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs, np.float64), q)) if xs else None
+
+
+# ------------------------------------------------------------------ reference arm
+def cpu_oracle_sample(budget_s=12.0, max_pairs=8):
+    """The FP64 oracle, as it stands, on whole 1024^2 pairs of the workload: as many as
+    fit in about budget_s seconds (at least one). Returns (fields/s, pairs, seconds, threads)."""
+    import oracle
+    from paper_1306_2461_gb300 import synth
+    oracle.build()
+    pairs = [synth.make_c2(H, W, seed=1 + 7919 * i) for i in range(2)]
+    t0 = time.perf_counter()
+    done = 0
+    while done < max_pairs:
+        p = pairs[done % len(pairs)]
+        oracle.flow(p.I1, p.I2, LEVELS, RADIUS, ITERS)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, oracle.threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1306_2461_gb300 import synth
+    oracle.build()
+    p = synth.make_c2(H, W, seed=1)
+    for _ in range(args.warmup):
+        oracle.flow(p.I1, p.I2, LEVELS, RADIUS, ITERS)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.flow(p.I1, p.I2, LEVELS, RADIUS, ITERS)
+        t.append(time.perf_counter() - t0)
+    total = sum(t)
+    val = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "H": H, "W": W, "levels": LEVELS,
+                                            "radius": RADIUS, "iterations": ITERS, "pairs_per_step": 1},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"one whole {H}x{W} pair per step, FP64 C oracle with OpenMP"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------ our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the single-pair and e2e legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    # the CPU oracle runs before the first GPU call (no fork after CUDA init)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample()
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1306_2461_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1306_2461_gb300 import of, synth
+
+    B = args.batch
+    src = [synth.make_c2(H, W, seed=1 + 7919 * (i + rank * DISTINCT)) for i in range(DISTINCT)]
+    dev = lambda a: torch.from_numpy(a.astype(np.int32)).cuda().to(torch.uint16)
+    I1 = [dev(src[i % DISTINCT].I1) for i in range(B)]
+    I2 = [dev(src[i % DISTINCT].I2) for i in range(B)]
+    stream = torch.cuda.Stream()
+    plan16 = of.Plan.make(H, W, LEVELS, RADIUS, ITERS, bits=BITS, storage="f16")
+    flows = [of.Flow(plan16) for _ in range(B)]
+    us = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(B)]
+    vs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(B)]
+
+    def step():
+        of.compute_batch(flows, I1, I2, us, vs, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    for f in flows:
+        if f.sync_status() != of.OF_OK:
+            raise RuntimeError("device status not OK after warm-up")
+
+    # timed region: K steps, events around every launch on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_host0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        t_host = time.perf_counter() - t_host0
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    fields = B * args.steps * world
+    value = fields / (total_ms / 1000.0)
+
+    extras = {}
+    if not args.no_extras:
+        extras = extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows)
+
+    # accuracy of the timed configuration on one pair (outside the timed region)
+    p0 = src[0]
+    u0 = us[0].cpu().double().numpy()
+    v0 = vs[0].cpu().double().numpy()
+    m = (RADIUS + 2) * 2 ** (LEVELS - 1)
+    e = np.sqrt((u0 - p0.u_gt) ** 2 + (v0 - p0.v_gt) ** 2)[m:-m, m:-m]
+    for f in flows:
+        if f.sync_status() != of.OF_OK:
+            raise RuntimeError("device status not OK after the timed region")
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    alg, alg_pyr, alg_it = algorithmic_bytes(H, W, LEVELS, ITERS, 2, 2)
+    peak, peak_kind = measured_peaks()
+    launch_ms = statistics.mean(step_ms)
+    achieved = alg * B / (launch_ms / 1000.0) / 1e9
+    khash = kernel_source_hash()
+    traffic = recorded_traffic(khash)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "f16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "bits": BITS, "levels": LEVELS, "radius": RADIUS,
+                   "iterations": ITERS, "pairs_per_step": B, "distinct_pairs": DISTINCT,
+                   "form": "batched persistent launch (of_compute_batch), CUDA graph",
+                   "l2": "no flush: per-step working set ~%.1f GB >> 129 MB L2" % (
+                       B * (of.workspace_bytes(plan16) + 4 * H * W) / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"step_p50": percentile(step_ms, 50), "step_p99": percentile(step_ms, 99),
+                       "step_max": max(step_ms)},
+        "mpix_iter_per_s": pixel_iterations(H, W, LEVELS, ITERS) * value / 1e6,
+        "epe_vs_ground_truth_px": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max()),
+                                   "margin_px": m},
+        "roofline": {"bound": "hbm", "kernel": "batch_kernel (persistent, whole method)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg * B,
+                     "algorithmic_bytes_per_field": {"total": alg, "pyramids": alg_pyr, "iterations": alg_it},
+                     "kernel_source_sha1": khash},
+        "gpu_launches": args.steps,
+        "host_wall_s": t_host,
+    }
+    if clocks:
+        line["clocks"] = clocks
+    line.update(extras)
+    if cpu is not None:
+        val, npairs, secs, threads = cpu
+        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{npairs} whole {H}x{W} pairs of the workload in {secs:.1f} s "
+                                          "(FP64 C oracle, OpenMP)"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows):
+    """Outside the headline timed region: the plain FP32 single-pair form (the comparison
+    the target names), and e2e through the C ABI with host buffers."""
+    out = {}
+    K = max(args.steps, 20)
+    # plain FP32 single pair, one of_compute (graph replay) per field
+    for storage in ("f32", "f16"):
+        plan = of.Plan.make(H, W, LEVELS, RADIUS, ITERS, bits=BITS, storage=storage)
+        with of.Flow(plan) as f, torch.cuda.stream(stream):
+            for _ in range(5):
+                f.compute(I1[0], I2[0], us[0], vs[0], stream=stream)
+            stream.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            for k in range(K):
+                evs[k][0].record(stream)
+                f.compute(I1[k % 4], I2[k % 4], us[0], vs[0], stream=stream)   # 4 = graph cache size
+                evs[k][1].record(stream)
+            stream.synchronize()
+            lat = [a.elapsed_time(b) for a, b in evs]
+            tot = evs[0][0].elapsed_time(evs[-1][1])
+        out[f"single_pair_{storage}"] = {"fields_per_s": K / (tot / 1000.0), "p50_ms": percentile(lat, 50),
+                                         "p99_ms": percentile(lat, 99)}
+    # e2e: host (pinned) frames in, device compute, host flow fields out, every step
+    B = len(flows)
+    h1 = [torch.from_numpy(src[i % len(src)].I1.astype(np.int32)).to(torch.uint16).pin_memory() for i in range(B)]
+    h2 = [torch.from_numpy(src[i % len(src)].I2.astype(np.int32)).to(torch.uint16).pin_memory() for i in range(B)]
+    hu = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(B)]
+    hv = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(B)]
+
+    def e2e_step():
+        for i in range(B):
+            I1[i].copy_(h1[i], non_blocking=True)
+            I2[i].copy_(h2[i], non_blocking=True)
+        of.compute_batch(flows, I1, I2, us, vs, stream=stream)
+        for i in range(B):
+            hu[i].copy_(us[i], non_blocking=True)
+            hv[i].copy_(vs[i], non_blocking=True)
+
+    Ke = max(3, args.steps // 2)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            e2e_step()
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(Ke):
+            e2e_step()
+        b.record(stream)
+        stream.synchronize()
+    ms = a.elapsed_time(b)
+    out["e2e"] = {"value": B * Ke / (ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": B * 2 * H * W * 2,
+                  "d2h_bytes_per_step": B * 2 * H * W * 4, "steps": Ke,
+                  "path": "pinned host frames -> of_compute_batch -> pinned host u, v (one stream)"}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * of.h -- C ABI of libof.so: dense pyramidal Lucas-Kanade optical flow on one GPU.
+ *
+ * The method is the one of Gautier & Aider, "Real-time planar flow velocity
+ * measurements using an optical flow algorithm implemented on GPU"
+ * (arXiv:1306.2461), Sect. 2.4: two camera images of a region of interest, a
+ * pyramid whose images shrink by 4 in area per level, an iterative Gauss-Newton
+ * minimisation of a windowed sum of squared differences (window radius r) on each
+ * level starting from zero displacement at the top, each level's result
+ * propagated as the starting estimate of the next finer level; one displacement
+ * vector per pixel.
+ *
+ * Conventions shared by every call:
+ *  - Images are row-major, pitch = W elements, 8-bit (uint8) or up to 16-bit
+ *    (uint16) camera counts. Displacements are FP32 pixels, returned as two planes
+ *    u (columns, positive to the right) and v (rows, positive downwards), pitch W,
+ *    such that I1(x) ~ I2(x + u(x)).
+ *  - Pointers named "device" must be device (or managed) memory of the current
+ *    CUDA device; the library never copies them. The caller owns them and keeps
+ *    them valid until the work queued on `stream` has completed.
+ *  - Calls are asynchronous with respect to the host unless stated otherwise.
+ *    Arguments are validated on the host before anything is queued; a call that
+ *    returns an error has queued nothing.
+ *  - Every call returns an of_status code (0 = OF_OK) and never throws.
+ *  - A handle is not thread-safe: one handle per camera stream, used by one host
+ *    thread at a time. Different handles may be used concurrently.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ */
+#ifndef OF_H_
+#define OF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *of_stream_t; /* identical to cudaStream_t */
+
+typedef enum of_status {
+    OF_OK = 0,
+    OF_EINVAL = -1,   /* an argument or the plan is out of range */
+    OF_ENOMEM = -2,   /* device allocation failed, or the HBM budget is exceeded */
+    OF_ECUDA = -3,    /* a CUDA runtime call failed (launch, copy, graph) */
+    OF_EDEVICE = -4,  /* a kernel reported a failed internal check */
+    OF_ETIMEOUT = -5, /* a bounded device-side wait ran out */
+    OF_ESTATE = -6,   /* the call needs state the handle does not have */
+    OF_EBUSY = -7     /* a server queue or slot pool is full */
+} of_status;
+
+typedef enum of_in_format { OF_U8 = 0, OF_U16 = 1 } of_in_format;
+
+/* Precision in which the pyramids are stored in HBM. Window sums and the 2x2
+ * solve always accumulate in FP32 (FP64 for ill-conditioned pixels). */
+typedef enum of_storage { OF_F32 = 0, OF_F16 = 1, OF_BF16 = 2 } of_storage;
+
+/* plan.flags */
+#define OF_FLAG_NO_GRAPH 0x1u /* launch kernels one by one instead of replaying a CUDA graph */
+
+/*
+ * Problem statement (Sect. 2.4): image size of the region of interest, number of
+ * pyramid levels n_lev and iterations per level n_iter (the two parameters that
+ * set the speed, Eq. 1 and Table 1), window radius r.
+ */
+typedef struct of_plan {
+    int32_t H, W;       /* image size in pixels, 1..32768 each, H*W <= 2^28 */
+    int32_t levels;     /* pyramid levels including full resolution, 1..16 */
+    int32_t radius;     /* window radius r: box of (2r+1)^2 pixels, 1..16 */
+    int32_t iterations; /* Gauss-Newton iterations per level, 1..1000 */
+    int32_t in_format;  /* OF_U8 or OF_U16 */
+    int32_t in_bits;    /* significant bits of the input, 1..8 (U8) or 1..16 (U16) */
+    int32_t storage;    /* OF_F32, OF_F16 or OF_BF16 */
+    float fp64_cond;    /* a pixel whose window matrix has tr^2/det above this value is
+                           solved in FP64; 0 = never (FP32 only). Default 1e3. */
+    uint32_t flags;     /* OF_FLAG_* */
+} of_plan;
+
+typedef struct of_ctx *of_handle;
+
+/* Fill *p with defaults for an H x W problem: levels 3, radius 4, iterations 5,
+ * OF_U8 with 8 bits, OF_F32 storage, fp64_cond 1e3, no flags. Host only. */
+void of_plan_init(of_plan *p, int32_t H, int32_t W);
+
+/* Check every field of *p against the ranges above. Host only.
+ * Returns OF_OK or OF_EINVAL (p == NULL included). */
+int of_plan_validate(const of_plan *p);
+
+/* Eq. 1 (Sect. 2.4): the pyramid should satisfy max_disp / 2^(levels-1) < 3 px.
+ * Sets *ok to 1 if it does for the given maximum displacement (pixels, at full
+ * resolution), 0 if not. Advisory only: of_create accepts either. Host only. */
+int of_plan_check(const of_plan *p, float max_disp_px, int *ok);
+
+/* Size of pyramid level `level` (0 = full resolution): each level has
+ * ceil(n/2) pixels along an axis of n pixels at the level below (Sect. 2.4, area
+ * reduced by 4 per level). Host only. OF_EINVAL if level is outside [0, levels). */
+int of_level_size(const of_plan *p, int32_t level, int32_t *Hl, int32_t *Wl);
+
+/* Bytes of device memory of_create allocates for this plan (both pyramids, two
+ * flow buffers, a status word), for admission against an HBM budget. Host only. */
+int of_workspace_bytes(const of_plan *p, size_t *bytes);
+
+/* Validate the plan and allocate the workspace on the current CUDA device.
+ * On success *out receives the handle; on failure *out is set to NULL and nothing
+ * is left allocated. OF_EINVAL (bad plan or out == NULL), OF_ENOMEM, OF_ECUDA. */
+int of_create(const of_plan *p, of_handle *out);
+
+/*
+ * Compute the displacement field from I1 to I2 (Sect. 2.4).
+ *  I1, I2: device, H*W elements of the plan's input format (uint8 or uint16).
+ *          I1 == NULL reuses the pyramid of the previous call's I2 on this handle
+ *          as the first image: with a time-resolved camera, each field then needs
+ *          only one new image to be processed (computing scheme 1 of Sect. 2.4).
+ *          OF_ESTATE if the handle has no previous I2.
+ *  u, v:   device, H*W floats each, written by the last kernel of the call.
+ *  stream: the work is queued on it; buffers must outlive the stream's progress.
+ * Returns OF_EINVAL (NULL handle, I2, u or v), OF_ESTATE, OF_ECUDA. Device-side
+ * failures are reported by of_sync_status.
+ */
+int of_compute(of_handle h, const void *I1, const void *I2, float *u, float *v, of_stream_t stream);
+
+/*
+ * Compute n independent fields in one persistent launch (fields are independent,
+ * Sect. 3.3, so they can share the GPU). hs[i] are handles whose plans have equal
+ * levels, radius, iterations, in_format, in_bits and storage (sizes may differ);
+ * a handle may appear at most once. I1s[i] may be NULL (reuse, as in of_compute).
+ * All pointers as in of_compute. n == 0 is a no-op. OF_EINVAL on mismatched plans,
+ * repeated handles or NULL pointers; OF_ESTATE as in of_compute.
+ * The results are those of n separate of_compute calls.
+ */
+int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
+                     float *const *us, float *const *vs, of_stream_t stream);
+
+/* Wait for the handle's last queued work, then read and clear its device status
+ * word. Returns OF_OK, OF_EDEVICE or OF_ETIMEOUT from the device, or OF_ECUDA. */
+int of_sync_status(of_handle h);
+
+/* Release the workspace. Waits for the handle's queued work first. NULL is a no-op. */
+int of_destroy(of_handle h);
+
+/* Copy pyramid level `level` of image `which` (0 = the first image of the last
+ * compute, 1 = the second) into dst (device, Hl*Wl floats, pitch Wl), converted to
+ * FP32. Used to check the pyramid step. OF_ESTATE before the first compute. */
+int of_get_level(of_handle h, int32_t which, int32_t level, float *dst, of_stream_t stream);
+
+/* The window-sum step alone (Sect. 2.4, window of radius r): out[c] = sum of ch[c]
+ * over the (2r+1)^2 box around each pixel, zero outside the image, for the 5
+ * planes c = 0..4. ch, out: device, 5*H*W floats (plane c at offset c*H*W).
+ * Same device code and summation order as inside the fused iteration. */
+int of_window_sums(const float *ch, int32_t H, int32_t W, int32_t r, float *out, of_stream_t stream);
+
+/* Test hook for bounded device waits: launches one kernel that waits for a device
+ * flag which nothing sets, giving up after about timeout_us microseconds. Blocks
+ * until it returns and reports OF_ETIMEOUT (the expected outcome) or OF_ECUDA. */
+int of_debug_wait_timeout(int32_t timeout_us);
+
+/* Static text for a status code. */
+const char *of_status_string(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int of_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OF_H_ */

@@ -1,0 +1,65 @@
+// Host-side engine state of libof: the handle, its workspace layout, graph cache.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/of.h"
+
+namespace of {
+
+constexpr int MAX_LEVELS = 16;
+constexpr int GRAPH_CACHE = 4;
+
+struct Layout {
+    int levels;
+    int H[MAX_LEVELS], W[MAX_LEVELS], pitch[MAX_LEVELS];
+    size_t level_off[MAX_LEVELS];   // byte offset of each level inside a pyramid slot
+    size_t pyr_bytes;               // one pyramid slot
+    size_t flow_bytes;              // one float2 flow buffer (level 0, pitched)
+    size_t total;
+};
+
+// A replayable launch sequence for one combination of caller pointers and slots.
+struct GraphEntry {
+    const void *I1, *I2;
+    float *u, *v;
+    int s1, s2;
+    cudaGraphExec_t exec;
+    uint64_t last_use;
+};
+
+void layout_plan(const of_plan &p, Layout &L);
+
+}  // namespace of
+
+struct of_ctx {
+    of_plan plan;
+    of::Layout lay;
+    int device = 0;
+    char *ws = nullptr;              // the one workspace allocation
+    char *pyr[2] = {nullptr, nullptr};
+    float2 *flow[2] = {nullptr, nullptr};
+    int *status = nullptr;           // device status word
+    cudaEvent_t done = nullptr;      // recorded after each compute
+    cudaStream_t ctl = nullptr;      // private stream for status reads
+    bool has_prev = false;           // a previous second image's pyramid is resident
+    int prev_slot = 1;
+    int last_s1 = 0, last_s2 = 1;
+    bool computed = false;
+    of::GraphEntry graphs[of::GRAPH_CACHE] = {};
+    int n_graphs = 0;
+    uint64_t use_clock = 0;
+};
+
+namespace of {
+
+cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, float *v, int s1, int s2,
+                         cudaStream_t st);
+// Queue one pair through a cached CUDA graph when the stream allows it, else directly.
+int run_pair(of_ctx *h, const void *I1, const void *I2, float *u, float *v, int s1, int s2, cudaStream_t st);
+void drop_graphs(of_ctx *h);
+cudaError_t configure_batch_kernels();
+
+}  // namespace of

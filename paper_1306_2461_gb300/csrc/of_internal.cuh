@@ -1,0 +1,117 @@
+// Internal declarations of libof: storage types, level descriptors, kernel launchers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/of.h"
+
+namespace of {
+
+// Device status word values (written by kernels, read by of_sync_status).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_INDEX = 2 };
+
+// ---------------------------------------------------------------- storage types
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float to_f(float x) { return x; }
+    static __device__ __forceinline__ float from_f(float x) { return x; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+    static __device__ __forceinline__ __half from_f(float x) { return __float2half_rn(x); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+    static __device__ __forceinline__ __nv_bfloat16 from_f(float x) { return __float2bfloat16_rn(x); }
+};
+
+inline int storage_bytes(int storage) { return storage == OF_F32 ? 4 : 2; }
+
+// Element type of one pyramid level. Level 0 keeps the camera's integer format (exact,
+// at most 2 bytes per pixel); the reduced levels use the plan's storage precision.
+enum ElemType : int { ET_U8 = 0, ET_U16 = 1, ET_F32 = 2, ET_F16 = 3, ET_BF16 = 4 };
+inline int elem_bytes(int et) { return et == ET_U8 ? 1 : (et == ET_F32 ? 4 : 2); }
+inline int raw_elem(int in_format) { return in_format == OF_U8 ? ET_U8 : ET_U16; }
+inline int storage_elem(int storage) { return storage == OF_F32 ? ET_F32 : (storage == OF_F16 ? ET_F16 : ET_BF16); }
+inline int level_elem(const of_plan &p, int level) { return level == 0 ? raw_elem(p.in_format) : storage_elem(p.storage); }
+
+template <typename T> __device__ __forceinline__ T to_elem(float x);
+template <> __device__ __forceinline__ float to_elem<float>(float x) { return x; }
+template <> __device__ __forceinline__ __half to_elem<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_elem<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ uint8_t to_elem<uint8_t>(float x) { return (uint8_t)__float2uint_rn(x); }
+template <> __device__ __forceinline__ uint16_t to_elem<uint16_t>(float x) { return (uint16_t)__float2uint_rn(x); }
+
+// One image level in HBM: row-major, `pitch` elements per row.
+struct Level {
+    void *ptr;
+    int32_t H, W, pitch;
+};
+
+// Flow input modes of one iteration.
+enum FlowMode : int {
+    FLOW_ZERO = 0,     // coarsest level, first iteration: u = v = 0
+    FLOW_SAME = 1,     // previous iterate on this level
+    FLOW_UPSAMPLE = 2  // first iteration of a finer level: 2 * bilinear(coarse, x/2, y/2)
+};
+
+// Arguments of one Gauss-Newton iteration on one level of one pair.
+struct IterArgs {
+    const void *I1;          // level image of the first frame (storage type)
+    const void *I2;          // level image of the second frame
+    int32_t H, W, pitch;     // level size, image pitch (elements)
+    const float2 *fin;       // input flow (FLOW_SAME: this level; FLOW_UPSAMPLE: coarse level)
+    int32_t fin_pitch;       // float2 elements per row of fin
+    int32_t Hc, Wc;          // coarse level size (FLOW_UPSAMPLE)
+    int32_t mode;            // FlowMode
+    float2 *fout;            // output flow (interleaved), or NULL when writing u/v planes
+    int32_t fout_pitch;
+    float *u_out, *v_out;    // final planes, pitch W (used when fout == NULL)
+    int32_t tiles_x;         // tiles along x (for flattened work lists)
+    int32_t tiles;           // tiles in this level
+};
+
+// Arguments of one pyramid reduction (both images of a pair at once).
+struct PyrArgs {
+    const void *src[2];      // raw input (first pass) or level l (storage type)
+    void *dst0[2];           // level 0 copy of the raw input (first pass; NULL otherwise)
+    void *dst[2];            // level l+1 output (NULL when levels == 1 in the first pass)
+    int32_t H, W;            // source size
+    int32_t src_pitch;       // elements
+    int32_t dst0_pitch;
+    int32_t Ho, Wo, dst_pitch;
+    int32_t first_image;     // 0: both images, 1: only the second (first reused)
+    int32_t tiles_x, tiles;  // output tiles of one image
+};
+
+// Tile shapes.
+constexpr int LK_TW = 32;    // iteration output tile width (one warp)
+constexpr int LK_TH = 32;    // iteration output tile height
+constexpr int LK_THREADS = 256;
+constexpr int PYR_TW = 32;   // pyramid output tile
+constexpr int PYR_TH = 16;
+constexpr int PYR_THREADS = 256;
+constexpr int MAX_RADIUS = 16;
+
+inline size_t lk_smem_bytes(int r) {
+    const int RH = LK_TH + 2 * r, RW = LK_TW + 2 * r;
+    return sizeof(float) * 5 * ((size_t)RH * RW + (size_t)RH * LK_TW);
+}
+
+// ------------------------------------------------------------------- launchers
+// All return cudaGetLastError() of their launch.
+cudaError_t launch_pyr_first(const PyrArgs &a, int in_format, int storage, cudaStream_t s);
+cudaError_t launch_pyr_down(const PyrArgs &a, int storage, cudaStream_t s);
+cudaError_t launch_lk_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s);
+cudaError_t launch_window_sums(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
+cudaError_t launch_level_to_f32(const Level &l, int elem, float *dst, cudaStream_t s);
+cudaError_t launch_wait_timeout(int *flag, int *status, long long timeout_ns, cudaStream_t s);
+cudaError_t configure_lk_kernels();
+
+}  // namespace of

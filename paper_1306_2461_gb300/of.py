@@ -1,0 +1,241 @@
+"""ctypes binding of libof.so (include/of.h). Argument marshalling only.
+
+Every step of the flow computation runs in the CUDA library; this module checks tensor
+shapes and dtypes, passes device pointers and the current CUDA stream, and turns status
+codes into exceptions. PyTorch provides device memory and streams. There is no CPU
+fallback: if libof.so is missing or cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libof.so")
+
+OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_EDEVICE, OF_ETIMEOUT, OF_ESTATE, OF_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+OF_U8, OF_U16 = 0, 1
+OF_F32, OF_F16, OF_BF16 = 0, 1, 2
+OF_FLAG_NO_GRAPH = 0x1
+STORAGE = {"f32": OF_F32, "f16": OF_F16, "bf16": OF_BF16}
+
+
+class OfError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {_lib.of_status_string(status).decode()} ({status})")
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("radius", ctypes.c_int32), ("iterations", ctypes.c_int32), ("in_format", ctypes.c_int32),
+                ("in_bits", ctypes.c_int32), ("storage", ctypes.c_int32), ("fp64_cond", ctypes.c_float),
+                ("flags", ctypes.c_uint32)]
+
+    @classmethod
+    def make(cls, H, W, levels=3, radius=4, iterations=5, bits=8, storage="f32", fp64_cond=1e3, flags=0):
+        p = cls()
+        _lib.of_plan_init(ctypes.byref(p), int(H), int(W))
+        p.levels, p.radius, p.iterations = int(levels), int(radius), int(iterations)
+        p.in_format = OF_U8 if bits <= 8 else OF_U16
+        p.in_bits = int(bits)
+        p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        p.fp64_cond = float(fp64_cond)
+        p.flags = int(flags)
+        return p
+
+    def __repr__(self):
+        return (f"Plan(H={self.H}, W={self.W}, levels={self.levels}, radius={self.radius}, "
+                f"iterations={self.iterations}, in_format={self.in_format}, in_bits={self.in_bits}, "
+                f"storage={self.storage}, fp64_cond={self.fp64_cond}, flags={self.flags})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1306_2461_gb300.build` "
+                          "(the flow computation has no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, vp, pp = ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)
+    P = ctypes.POINTER(Plan)
+    sig = {
+        "of_plan_init": (None, [P, i32, i32]),
+        "of_plan_validate": (ctypes.c_int, [P]),
+        "of_plan_check": (ctypes.c_int, [P, ctypes.c_float, ctypes.POINTER(ctypes.c_int)]),
+        "of_level_size": (ctypes.c_int, [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "of_workspace_bytes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_size_t)]),
+        "of_create": (ctypes.c_int, [P, pp]),
+        "of_compute": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+        "of_compute_batch": (ctypes.c_int, [i32, pp, pp, pp, pp, pp, vp]),
+        "of_sync_status": (ctypes.c_int, [vp]),
+        "of_destroy": (ctypes.c_int, [vp]),
+        "of_get_level": (ctypes.c_int, [vp, i32, i32, vp, vp]),
+        "of_window_sums": (ctypes.c_int, [vp, i32, i32, i32, vp, vp]),
+        "of_debug_wait_timeout": (ctypes.c_int, [i32]),
+        "of_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "of_version": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != OF_OK:
+        raise OfError(rc, what)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ------------------------------------------------------------------ host helpers
+def plan_validate(p: Plan) -> int:
+    return _lib.of_plan_validate(ctypes.byref(p))
+
+
+def plan_check(p: Plan, max_disp_px: float) -> bool:
+    ok = ctypes.c_int()
+    _check(_lib.of_plan_check(ctypes.byref(p), float(max_disp_px), ctypes.byref(ok)), "of_plan_check")
+    return bool(ok.value)
+
+
+def level_size(p: Plan, level: int) -> tuple[int, int]:
+    h, w = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.of_level_size(ctypes.byref(p), int(level), ctypes.byref(h), ctypes.byref(w)), "of_level_size")
+    return h.value, w.value
+
+
+def workspace_bytes(p: Plan) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.of_workspace_bytes(ctypes.byref(p), ctypes.byref(n)), "of_workspace_bytes")
+    return n.value
+
+
+def version() -> int:
+    return _lib.of_version()
+
+
+# ------------------------------------------------------------------- the handle
+def _img_ptr(t: torch.Tensor | None, p: Plan, name: str) -> int | None:
+    if t is None:
+        return None
+    want = torch.uint8 if p.in_format == OF_U8 else torch.uint16
+    if t.dtype != want or not t.is_cuda or tuple(t.shape) != (p.H, p.W) or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous CUDA {want} tensor of shape ({p.H}, {p.W}), "
+                         f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+    return t.data_ptr()
+
+
+def _flow_ptr(t: torch.Tensor, p: Plan, name: str) -> int:
+    if t.dtype != torch.float32 or not t.is_cuda or tuple(t.shape) != (p.H, p.W) or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous CUDA float32 tensor of shape ({p.H}, {p.W})")
+    return t.data_ptr()
+
+
+class Flow:
+    """One of_create handle: the workspace of one plan on the current device."""
+
+    def __init__(self, plan: Plan):
+        self.plan = plan
+        h = ctypes.c_void_p()
+        _check(_lib.of_create(ctypes.byref(plan), ctypes.byref(h)), "of_create")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("handle destroyed")
+        return self._h
+
+    def compute(self, I1, I2, u=None, v=None, stream=None):
+        """Queue the flow I1 -> I2 on `stream` (default: torch's current stream).
+        I1 = None reuses the previous call's I2 pyramid. Returns (u, v)."""
+        p = self.plan
+        if u is None:
+            u = torch.empty((p.H, p.W), dtype=torch.float32, device=I2.device)
+        if v is None:
+            v = torch.empty((p.H, p.W), dtype=torch.float32, device=I2.device)
+        rc = _lib.of_compute(self.handle, _img_ptr(I1, p, "I1"), _img_ptr(I2, p, "I2"), _flow_ptr(u, p, "u"),
+                             _flow_ptr(v, p, "v"), _stream(stream))
+        _check(rc, "of_compute")
+        return u, v
+
+    def sync_status(self) -> int:
+        return _lib.of_sync_status(self.handle)
+
+    def get_level(self, which: int, level: int, stream=None) -> torch.Tensor:
+        Hl, Wl = level_size(self.plan, level)
+        out = torch.empty((Hl, Wl), dtype=torch.float32, device="cuda")
+        _check(_lib.of_get_level(self.handle, int(which), int(level), out.data_ptr(), _stream(stream)),
+               "of_get_level")
+        return out
+
+    def close(self):
+        if self._h is not None:
+            rc = _lib.of_destroy(self._h)
+            self._h = None
+            _check(rc, "of_destroy")
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None:
+                _lib.of_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _ptr_array(vals):
+    arr = (ctypes.c_void_p * max(1, len(vals)))()
+    for i, x in enumerate(vals):
+        arr[i] = x
+    return arr
+
+
+def compute_batch(flows, I1s, I2s, us=None, vs=None, stream=None):
+    """of_compute_batch over independent pairs. Returns the lists (us, vs)."""
+    n = len(flows)
+    if us is None:
+        us = [torch.empty((f.plan.H, f.plan.W), dtype=torch.float32, device="cuda") for f in flows]
+    if vs is None:
+        vs = [torch.empty((f.plan.H, f.plan.W), dtype=torch.float32, device="cuda") for f in flows]
+    hs = _ptr_array([f.handle.value for f in flows])
+    a1 = _ptr_array([_img_ptr(I1s[i], flows[i].plan, "I1") for i in range(n)])
+    a2 = _ptr_array([_img_ptr(I2s[i], flows[i].plan, "I2") for i in range(n)])
+    au = _ptr_array([_flow_ptr(us[i], flows[i].plan, "u") for i in range(n)])
+    av = _ptr_array([_flow_ptr(vs[i], flows[i].plan, "v") for i in range(n)])
+    _check(_lib.of_compute_batch(n, hs, a1, a2, au, av, _stream(stream)), "of_compute_batch")
+    return us, vs
+
+
+def window_sums(ch: torch.Tensor, r: int, stream=None) -> torch.Tensor:
+    """Box sums of 5 planes (5, H, W) float32 over the (2r+1)^2 window (zero outside)."""
+    if ch.dtype != torch.float32 or not ch.is_cuda or ch.dim() != 3 or ch.shape[0] != 5 or not ch.is_contiguous():
+        raise ValueError("ch: expected a contiguous CUDA float32 tensor of shape (5, H, W)")
+    out = torch.empty_like(ch)
+    _check(_lib.of_window_sums(ch.data_ptr(), ch.shape[1], ch.shape[2], int(r), out.data_ptr(), _stream(stream)),
+           "of_window_sums")
+    return out
+
+
+def debug_wait_timeout(timeout_us: int) -> int:
+    return _lib.of_debug_wait_timeout(int(timeout_us))

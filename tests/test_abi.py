@@ -1,0 +1,82 @@
+"""The C-ABI library: it loads, exports every entry point include/of.h declares, and its
+host-only calls (plan validation, Eq. 1, level sizes, workspace size) behave. No GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1306_2461_gb300 import build as of_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def of():
+    of_build.build()
+    from paper_1306_2461_gb300 import of as ofmod
+    return ofmod
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(of_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(of):
+    syms = declared_symbols()
+    assert "of_create" in syms and "of_compute" in syms and "of_destroy" in syms
+    lib = ctypes.CDLL(of.LIB_PATH)
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_plan_defaults_and_validation(of):
+    p = of.Plan.make(1024, 1024, 3, 4, 5, bits=12, storage="f16")
+    assert of.plan_validate(p) == of.OF_OK
+    for field, bad in [("H", 0), ("W", -3), ("levels", 0), ("levels", 17), ("radius", 0), ("radius", 17),
+                       ("iterations", 0), ("in_bits", 17), ("storage", 7), ("in_format", 5), ("flags", 0x80)]:
+        q = of.Plan.make(64, 64)
+        setattr(q, field, bad)
+        assert of.plan_validate(q) == of.OF_EINVAL, field
+    q = of.Plan.make(64, 64)
+    q.fp64_cond = float("nan")
+    assert of.plan_validate(q) == of.OF_EINVAL
+    q = of.Plan.make(32768, 32768)          # 2^30 pixels: above the 2^28 limit
+    assert of.plan_validate(q) == of.OF_EINVAL
+    assert of.plan_validate(of.Plan.make(1, 1, levels=1, radius=16)) == of.OF_OK
+
+
+def test_eq1_level_rule_matches_golden(of):
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "nlevels.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 10
+    for disp, levels, ok in rows:
+        p = of.Plan.make(512, 512, levels=int(levels))
+        assert of.plan_check(p, float(disp)) == bool(int(ok)), (disp, levels)
+
+
+def test_level_sizes_and_workspace(of):
+    p = of.Plan.make(383, 1791, levels=3)
+    assert [of.level_size(p, l) for l in range(3)] == [(383, 1791), (192, 896), (96, 448)]
+    with pytest.raises(of.OfError):
+        of.level_size(p, 3)
+    N = 1024 * 1024
+    flows = 2 * N * 8
+    # two pyramids: level 0 in the camera format (1 or 2 B/px), levels 1 and 2
+    # (1/4 + 1/16 of the pixels) at the storage precision (4 or 2 B/px)
+    for bits, raw in ((8, 1), (12, 2)):
+        for storage, s in (("f32", 4), ("f16", 2), ("bf16", 2)):
+            b = of.workspace_bytes(of.Plan.make(1024, 1024, bits=bits, storage=storage))
+            assert abs((b - flows) - 2 * N * (raw + s * 0.3125)) < 1e5, (bits, storage)
+
+
+def test_status_strings_and_version(of):
+    for s in range(-7, 1):
+        assert of.lib().of_status_string(s)
+    assert of.version() >= 100

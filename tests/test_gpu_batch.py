@@ -1,0 +1,125 @@
+"""The batched persistent form (of_compute_batch): the same fields as one of_compute per
+pair, bit for bit, and the oracle on sampled pairs, at the full sizes of the
+benchmark's launch configuration and of the mixed-size batch."""
+import numpy as np
+import pytest
+
+from paper_1306_2461_gb300 import synth
+from helpers import parity_check, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def of():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_2461_gb300 import build
+    build.build()
+    from paper_1306_2461_gb300 import of as ofmod
+    return ofmod
+
+
+def single(of, plan, I1, I2):
+    import torch
+    with of.Flow(plan) as f:
+        u, v = f.compute(I1, I2)
+        torch.cuda.synchronize()
+        assert f.sync_status() == of.OF_OK
+    return u, v
+
+
+def oracle_check(oracle_mod, pair, u, v, L, r, n, storage):
+    parity_check(u.cpu().double().numpy(), v.cpu().double().numpy(), pair, oracle_mod, L, r, n, storage,
+                 f"{pair.I1.shape[0]}x{pair.I1.shape[1]}")
+
+
+def test_bench_configuration_full_size(of, oracle_mod):
+    # 64 pairs of 1024^2 12-bit frames, FP16 storage, 3 levels, r = 4, 5 iterations:
+    # the launch the benchmark times (8 distinct pairs cycled, as there)
+    import torch
+    B, D = 64, 8
+    src = [synth.make_c2(1024, 1024, seed=1 + 7919 * i) for i in range(D)]
+    plan = of.Plan.make(1024, 1024, 3, 4, 5, bits=12, storage="f16")
+    flows = [of.Flow(plan) for _ in range(B)]
+    I1 = [to_dev(src[i % D].I1) for i in range(B)]
+    I2 = [to_dev(src[i % D].I2) for i in range(B)]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):                    # second call replays the cached graph
+            us, vs = of.compute_batch(flows, I1, I2, stream=s)
+    s.synchronize()
+    assert all(f.sync_status() == of.OF_OK for f in flows)
+    for i in range(D):
+        u1, v1 = single(of, plan, I1[i], I2[i])
+        for j in range(i, B, D):               # every copy of pair i
+            assert torch.equal(us[j], u1) and torch.equal(vs[j], v1), j
+    for i in (0, 5):
+        oracle_check(oracle_mod, src[i], us[i], vs[i], 3, 4, 5, "f16")
+    for f in flows:
+        f.close()
+
+
+def test_mixed_size_batch_64_pairs(of, oracle_mod):
+    # 64 uint8 pairs drawn from 256^2, 512^2, 1024^2 and 1024x2048, uniform + vortex
+    # flows, 3 levels, r = 4, 5 iterations, FP16 storage
+    import torch
+    pairs = synth.make_batch(64, seed=3)
+    plans = [of.Plan.make(*p.shape, 3, 4, 5, bits=8, storage="f16") for p in pairs]
+    flows = [of.Flow(pl) for pl in plans]
+    I1 = [to_dev(p.I1) for p in pairs]
+    I2 = [to_dev(p.I2) for p in pairs]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        us, vs = of.compute_batch(flows, I1, I2, stream=s)
+    s.synchronize()
+    assert all(f.sync_status() == of.OF_OK for f in flows)
+    for i in range(0, 64, 5):
+        u1, v1 = single(of, plans[i], I1[i], I2[i])
+        assert torch.equal(us[i], u1) and torch.equal(vs[i], v1), i
+    smallest = min(range(64), key=lambda i: pairs[i].I1.size)
+    for i in (smallest, 7):
+        oracle_check(oracle_mod, pairs[i], us[i], vs[i], 3, 4, 5, "f16")
+    for f in flows:
+        f.close()
+
+
+def test_batch_with_reused_first_image(of):
+    # scheme 1 inside a batch: half the pairs reuse their previous second image
+    import torch
+    streams = [synth.ParticleStream(160, 224, seed=k) for k in range(4)]
+    frames = []
+    for st in streams:
+        fr = []
+        for _ in range(3):
+            fr.append(to_dev(st.frame()))
+            st.advance()
+        frames.append(fr)
+    plan = of.Plan.make(160, 224, 3, 4, 3, bits=12, storage="f16")
+    flows = [of.Flow(plan) for _ in range(4)]
+    of.compute_batch(flows, [f[0] for f in frames], [f[1] for f in frames])
+    ub, vb = of.compute_batch(flows, [None, frames[1][1], None, frames[3][1]], [f[2] for f in frames])
+    torch.cuda.synchronize()
+    for k in range(4):
+        u1, v1 = single(of, plan, frames[k][1], frames[k][2])
+        assert torch.equal(ub[k], u1) and torch.equal(vb[k], v1), k
+    for f in flows:
+        f.close()
+
+
+def test_batch_rejects_mixed_methods_and_repeats(of):
+    import torch
+    a = of.Flow(of.Plan.make(64, 64, 3, 4, 5))
+    b = of.Flow(of.Plan.make(64, 64, 3, 5, 5))
+    I = torch.zeros((64, 64), dtype=torch.uint8, device="cuda")
+    with pytest.raises(of.OfError) as ei:
+        of.compute_batch([a, b], [I, I], [I, I])
+    assert ei.value.status == of.OF_EINVAL
+    with pytest.raises(of.OfError) as ei:
+        of.compute_batch([a, a], [I, I], [I, I])
+    assert ei.value.status == of.OF_EINVAL
+    c = of.Flow(of.Plan.make(64, 64, 3, 4, 5))
+    with pytest.raises(of.OfError) as ei:
+        of.compute_batch([a, c], [I, None], [I, I])
+    assert ei.value.status == of.OF_ESTATE

@@ -1,0 +1,202 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances on valid pixels (helpers.parity_check states which pixels are valid and
+why): FP32 storage max |du|,|dv| <= 1e-3 px; FP16 storage <= 2e-2 px max and
+<= 5e-3 px RMS. Ragged and degenerate shapes use a well-conditioned texture and
+compare every pixel.
+"""
+import numpy as np
+import pytest
+
+from paper_1306_2461_gb300 import synth
+from helpers import compare, epe, gpu_flow, parity_check, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def of():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_2461_gb300 import build
+    build.build()
+    from paper_1306_2461_gb300 import of as ofmod
+    return ofmod
+
+
+def check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label="", margin=None, workload=True):
+    return parity_check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label, margin, workload)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("H,W,L,r,n", [(256, 256, 2, 5, 4), (77, 301, 3, 4, 2), (1, 1, 1, 1, 1), (5, 3, 4, 10, 2)])
+def test_identical_images_exactly_zero(of, storage, H, W, L, r, n):
+    rng = np.random.default_rng(H * W)
+    I = rng.integers(0, 4096, (H, W)).astype(np.uint16)
+    u, v = gpu_flow((I, I), L, r, n, storage=storage, bits=12)
+    assert np.all(u == 0.0) and np.all(v == 0.0)
+
+
+@pytest.mark.parametrize("H,W,r", [(7, 9, 2), (3, 3, 5), (70, 45, 4), (33, 97, 16), (1, 1, 1), (64, 64, 10)])
+def test_window_sums_bitwise(of, H, W, r):
+    import torch
+    from scipy import signal
+    rng = np.random.default_rng(H * 7 + W + r)
+    ch = rng.integers(-2000, 2000, (5, H, W)).astype(np.float32)
+    out = of.window_sums(torch.from_numpy(ch).cuda(), r).cpu().numpy()
+    box = np.ones((2 * r + 1, 2 * r + 1))
+    for c in range(5):
+        ref = signal.convolve2d(ch[c].astype(np.float64), box, mode="same")
+        assert np.array_equal(out[c].astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("storage,atol", [("f32", 2e-3), ("f16", 2.0), ("bf16", 16.0)])
+def test_pyramid_levels_match_oracle(of, oracle_mod, storage, atol):
+    # level 0 is the camera image itself (exact); reduced levels carry the storage
+    # rounding: relative 2^-24 (f32), 2^-11 (f16), 2^-8 (bf16) of values <= 4095
+    import torch
+    p = synth.make_c2(300, 420, seed=5)
+    plan = of.Plan.make(300, 420, 4, 4, 1, bits=12, storage=storage)
+    with of.Flow(plan) as f:
+        u, v = f.compute(to_dev(p.I1), to_dev(p.I2))
+        torch.cuda.synchronize()
+        for which, img in ((0, p.I1), (1, p.I2)):
+            ref = oracle_mod.pyramid(img, 4)
+            for l in range(4):
+                got = f.get_level(which, l).cpu().double().numpy()
+                assert got.shape == ref[l].shape
+                if l == 0:
+                    assert np.array_equal(got, ref[0]), which
+                else:
+                    assert np.abs(got - ref[l]).max() <= atol, (which, l)
+
+
+def test_translation_pin_on_gpu(of, oracle_mod):
+    # the pins of the oracle hold for the CUDA path too (integer image of a texture)
+    d = (1.3, -0.7)
+    I1, I2 = synth.translated_texture_pair(160, 192, d, seed=1, amp=800.0, offset=2000.0)
+    I1 = np.rint(I1).astype(np.uint16)
+    I2 = np.rint(I2).astype(np.uint16)
+    u, v = gpu_flow((I1, I2), 2, 10, 10, storage="f32", bits=12)
+    m = 24
+    assert abs(u[m:-m, m:-m].mean() - d[0]) < 0.01 and abs(v[m:-m, m:-m].mean() - d[1]) < 0.01
+    check(u, v, (I1, I2), oracle_mod, 2, 10, 10, "f32", "texture", margin=0, workload=False)
+
+
+def test_c1_pair256_fp32(of, oracle_mod):
+    p = synth.make_c1()
+    u, v = gpu_flow(p, 2, 5, 4, "f32")
+    check(u, v, p, oracle_mod, 2, 5, 4, "f32", "256^2 u8")
+    rms, mx = epe(u, v, p, 14)
+    print(f"EPE vs ground truth: rms {rms:.4f} max {mx:.4f}")
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("H,W", [(384, 320), (1024, 1024)])
+def test_c2_vortex_shear(of, oracle_mod, storage, H, W):
+    p = synth.make_c2(H, W, seed=1)
+    u, v = gpu_flow(p, 3, 4, 5, storage)
+    check(u, v, p, oracle_mod, 3, 4, 5, storage, f"{H}x{W} u16")
+    rms, mx = epe(u, v, p, 24)
+    print(f"EPE vs ground truth: rms {rms:.4f} max {mx:.4f}")
+
+
+def test_c2_bf16_reported(of, oracle_mod):
+    # BF16 keeps 8 mantissa bits. No tolerance is stated for it; the check uses ten
+    # times the FP16 bounds and the error is reported.
+    p = synth.make_c2(512, 512, seed=1)
+    u, v = gpu_flow(p, 3, 4, 5, "bf16")
+    check(u, v, p, oracle_mod, 3, 4, 5, "bf16", "512x512 u16")
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("H,W,L,r,n", [(200, 150, 3, 4, 3), (37, 301, 2, 3, 2), (64, 64, 1, 10, 3),
+                                       (130, 66, 4, 2, 1), (97, 33, 2, 1, 2), (2, 9, 2, 2, 2), (5, 3, 4, 10, 2),
+                                       (1, 1, 1, 1, 1)])
+def test_ragged_and_degenerate_shapes_every_pixel(of, oracle_mod, storage, H, W, L, r, n):
+    # ragged tiles, images smaller than one tile or one window, more levels than the
+    # image can halve: every pixel, on a 12-bit texture (frequencies <= 1/6 cycles/px)
+    I1, I2 = synth.translated_texture_pair(H, W, (0.4, -0.3), seed=H + W, amp=800.0, offset=2000.0,
+                                           fmax=1.0 / 6.0)
+    I1 = np.rint(I1).astype(np.uint16)
+    I2 = np.rint(I2).astype(np.uint16)
+    u, v = gpu_flow((I1, I2), L, r, n, storage, bits=12)
+    check(u, v, (I1, I2), oracle_mod, L, r, n, storage, f"{H}x{W}", margin=0, workload=False)
+
+
+@pytest.mark.parametrize("H,W,L,r,n", [(200, 150, 3, 4, 3), (37, 301, 2, 3, 2), (130, 66, 4, 2, 1)])
+def test_ragged_particle_pairs_fp32(of, oracle_mod, H, W, L, r, n):
+    p = synth.make_c1(H, W, seed=H + W)
+    u, v = gpu_flow(p, L, r, n, "f32")
+    check(u, v, p, oracle_mod, L, r, n, "f32", f"{H}x{W}")
+
+
+def test_reuse_previous_pyramid_equals_explicit(of):
+    import torch
+    s = synth.ParticleStream(192, 256, seed=3)
+    frames = []
+    for _ in range(3):
+        frames.append(s.frame())
+        s.advance()
+    plan = of.Plan.make(192, 256, 3, 4, 3, bits=12, storage="f16")
+    with of.Flow(plan) as f, of.Flow(plan) as g:
+        d = [to_dev(x) for x in frames]
+        u1, v1 = f.compute(d[0], d[1])
+        u1, v1 = u1.clone(), v1.clone()
+        u2, v2 = f.compute(None, d[2])          # reuses frame 1's pyramid
+        ue, ve = g.compute(d[1], d[2])          # explicit pair (1, 2)
+        torch.cuda.synchronize()
+        assert torch.equal(u2, ue) and torch.equal(v2, ve)
+        assert not torch.equal(u1, u2)
+        with pytest.raises(of.OfError) as ei:
+            of.Flow(plan).compute(None, d[0])
+        assert ei.value.status == of.OF_ESTATE
+
+
+def test_graph_replay_equals_direct_launches(of):
+    import torch
+    p = synth.make_c2(256, 320, seed=9)
+    s = torch.cuda.Stream()
+    res = []
+    for flags in (0, of.OF_FLAG_NO_GRAPH):
+        plan = of.Plan.make(256, 320, 3, 4, 5, bits=12, storage="f16", flags=flags)
+        with of.Flow(plan) as f, torch.cuda.stream(s):
+            I1, I2 = to_dev(p.I1), to_dev(p.I2)
+            for _ in range(3):                  # replay the cached graph
+                u, v = f.compute(I1, I2, stream=s)
+            s.synchronize()
+            res.append((u.clone(), v.clone()))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+
+
+def test_batch_equals_single(of):
+    import torch
+    pairs = synth.make_batch(6, seed=3, sizes=((96, 128), (160, 160), (64, 200)))
+    flows = [of.Flow(of.Plan.make(*p.shape, 3, 4, 5, bits=8, storage="f16")) for p in pairs]
+    I1s = [to_dev(p.I1) for p in pairs]
+    I2s = [to_dev(p.I2) for p in pairs]
+    ub, vb = of.compute_batch(flows, I1s, I2s)
+    torch.cuda.synchronize()
+    for i, p in enumerate(pairs):
+        with of.Flow(of.Plan.make(*p.shape, 3, 4, 5, bits=8, storage="f16")) as g:
+            us, vs = g.compute(I1s[i], I2s[i])
+            torch.cuda.synchronize()
+        assert torch.equal(ub[i], us) and torch.equal(vb[i], vs), i
+    for f in flows:
+        f.close()
+
+
+def test_invalid_calls_are_rejected(of):
+    import ctypes
+    plan = of.Plan.make(64, 64)
+    with of.Flow(plan) as f:
+        assert of.lib().of_compute(f.handle, None, None, None, None, None) == of.OF_EINVAL
+    bad = of.Plan.make(0, 64)
+    h = ctypes.c_void_p()
+    assert of.lib().of_create(ctypes.byref(bad), ctypes.byref(h)) == of.OF_EINVAL and not h.value
+    assert of.lib().of_compute_batch(0, None, None, None, None, None, None) == of.OF_OK
+
+
+def test_bounded_device_wait_times_out(of):
+    assert of.debug_wait_timeout(2000) == of.OF_ETIMEOUT
