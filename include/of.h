@@ -131,6 +131,30 @@ int of_compute(of_handle h, const void *I1, const void *I2, float *u, float *v, 
 int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
                      float *const *us, float *const *vs, of_stream_t stream);
 
+/*
+ * of_compute without any device allocation. The paper has no counterpart: this is for
+ * callers that cannot call cudaMalloc once running, such as a real-time acquisition
+ * loop (cudaMalloc/cudaFree can synchronise the device and stall the camera pipeline)
+ * or a host application that owns all device memory through its own allocator.
+ * The workspace of of_create lives here in one static device array of
+ * OF_NOALLOC_MAX_BYTES (32 MiB: enough for one 1024 x 1024 pair at any storage),
+ * reserved on every GPU where the library's code is loaded and held until exit.
+ *  p:      the plan, as for of_create; plans whose of_workspace_bytes exceed
+ *          OF_NOALLOC_MAX_BYTES are rejected with OF_ENOMEM before anything is queued.
+ *  I1, I2, u, v, stream: as for of_compute, except that I1 must not be NULL (there is
+ *          no handle, so no previous pyramid to reuse): OF_EINVAL.
+ * Nothing is allocated, on the device or by a library routine: kernels are launched
+ * directly on `stream` (no graph), and the status word is cleared with a memset.
+ * The first call on a device, with that device current, looks up the array's device
+ * address and sets kernel attributes; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents: calls whose
+ * work overlaps on the GPU (different streams, or other host threads) race and give
+ * wrong results; serialise them on one stream.
+ * Returns OF_OK, OF_EINVAL, OF_ENOMEM or OF_ECUDA.
+ */
+#define OF_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)
+int of_compute_noalloc(const of_plan *p, const void *I1, const void *I2, float *u, float *v, of_stream_t stream);
+
 /* Wait for the handle's last queued work, then read and clear its device status
  * word. Returns OF_OK, OF_EDEVICE or OF_ETIMEOUT from the device, or OF_ECUDA. */
 int of_sync_status(of_handle h);
