@@ -57,6 +57,9 @@ typedef enum of_storage { OF_F32 = 0, OF_F16 = 1, OF_BF16 = 2 } of_storage;
 
 /* plan.flags */
 #define OF_FLAG_NO_GRAPH 0x1u /* launch kernels one by one instead of replaying a CUDA graph */
+#define OF_FLAG_STAGE_I2 0x2u /* stage each tile's I2 footprint in shared memory with bulk async
+                                 copies instead of gathering the taps from global memory (same
+                                 results; a different trade between latency and work) */
 
 /*
  * Problem statement (Sect. 2.4): image size of the region of interest, number of

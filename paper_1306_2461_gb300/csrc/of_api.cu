@@ -32,7 +32,7 @@ int configure_device()
     std::lock_guard<std::mutex> lk(g_dev_mu);
     if (dev < 0 || dev >= 256) return OF_ECUDA;
     if (g_dev_configured[dev]) return OF_OK;
-    if (configure_lk_kernels() != cudaSuccess || configure_batch_kernels() != cudaSuccess) return OF_ECUDA;
+    if (configure_lk_kernels() != cudaSuccess) return OF_ECUDA;
     g_dev_configured[dev] = true;
     return OF_OK;
 }
@@ -148,6 +148,8 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
             }
             a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
             a.tiles = a.tiles_x * ((a.H + LK_TH - 1) / LK_TH);
+            a.status = h->status;
+            a.stage_i2 = (p.flags & OF_FLAG_STAGE_I2) ? 1 : 0;
             if ((e = launch_lk_iter(a, level_elem(p, l), p.radius, p.fp64_cond, st)) != cudaSuccess) return e;
             cur = 1 - cur;
         }
@@ -193,7 +195,7 @@ int of_plan_validate(const of_plan *p)
     }
     if (p->storage != OF_F32 && p->storage != OF_F16 && p->storage != OF_BF16) return OF_EINVAL;
     if (!(p->fp64_cond >= 0.0f) || isinf(p->fp64_cond)) return OF_EINVAL;
-    if (p->flags & ~OF_FLAG_NO_GRAPH) return OF_EINVAL;
+    if (p->flags & ~(OF_FLAG_NO_GRAPH | OF_FLAG_STAGE_I2)) return OF_EINVAL;
     return OF_OK;
 }
 

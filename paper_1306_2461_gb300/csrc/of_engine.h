@@ -60,6 +60,5 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
 // Queue one pair through a cached CUDA graph when the stream allows it, else directly.
 int run_pair(of_ctx *h, const void *I1, const void *I2, float *u, float *v, int s1, int s2, cudaStream_t st);
 void drop_graphs(of_ctx *h);
-cudaError_t configure_batch_kernels();
 
 }  // namespace of

@@ -75,6 +75,8 @@ struct IterArgs {
     float *u_out, *v_out;    // final planes, pitch W (used when fout == NULL)
     int32_t tiles_x;         // tiles along x (for flattened work lists)
     int32_t tiles;           // tiles in this level
+    int *status;             // the handle's device status word (errors only)
+    int32_t stage_i2;        // stage the tile's I2 footprint in shared memory (fixed-radius tile)
 };
 
 // Arguments of one pyramid reduction (both images of a pair at once).
@@ -91,7 +93,7 @@ struct PyrArgs {
 };
 
 // Tile shapes.
-constexpr int LK_TW = 32;    // iteration output tile width (one warp)
+constexpr int LK_TW = 64;    // iteration output tile width
 constexpr int LK_TH = 32;    // iteration output tile height
 constexpr int LK_THREADS = 256;
 constexpr int PYR_TW = 32;   // pyramid output tile
@@ -99,10 +101,9 @@ constexpr int PYR_TH = 16;
 constexpr int PYR_THREADS = 256;
 constexpr int MAX_RADIUS = 16;
 
-inline size_t lk_smem_bytes(int r) {
-    const int RH = LK_TH + 2 * r, RW = LK_TW + 2 * r;
-    return sizeof(float) * 5 * ((size_t)RH * RW + (size_t)RH * LK_TW);
-}
+// Window radii with a kernel specialised at compile time (the workloads' and the
+// paper's radii); any other radius runs the generic kernel.
+#define OF_RADII(X) X(2) X(3) X(4) X(5) X(6) X(8) X(10)
 
 // ------------------------------------------------------------------- launchers
 // All return cudaGetLastError() of their launch.
@@ -110,8 +111,17 @@ cudaError_t launch_pyr_first(const PyrArgs &a, int in_format, int storage, cudaS
 cudaError_t launch_pyr_down(const PyrArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_lk_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s);
 cudaError_t launch_window_sums(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
+void *batch_kernel_for(int in_format, int storage, int radius);
+size_t batch_smem_bytes(int radius);
 cudaError_t launch_level_to_f32(const Level &l, int elem, float *dst, cudaStream_t s);
 cudaError_t launch_wait_timeout(int *flag, int *status, long long timeout_ns, cudaStream_t s);
-cudaError_t configure_lk_kernels();
+cudaError_t configure_lk_kernels();   // all kernels with dynamic shared memory, current device
+
+// Per-radius instantiations (radius_<R>.cu; R = 0 is the generic kernel).
+template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
+template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
+template <int R> void *batch_kernel_ptr(int in_format, int storage);
+template <int R> cudaError_t radius_configure();
+template <int R> size_t radius_smem_bytes(int r);
 
 }  // namespace of

@@ -2,6 +2,9 @@
 // kernel: one pyramid-reduction tile and one Gauss-Newton iteration tile.
 #pragma once
 
+#include <climits>
+
+#include "async_copy.cuh"
 #include "of_internal.cuh"
 
 namespace of {
@@ -206,21 +209,22 @@ __device__ __forceinline__ bool solve2(const float s[5], float fp64_cond, float 
     return true;
 }
 
-inline __host__ __device__ int lk_smem_floats(int r)
+inline __host__ __device__ int lk_smem_floats(int r)   // generic tile
 {
     const int RH = LK_TH + 2 * r, RW = LK_TW + 2 * r;
     return 5 * (RH * RW + RH * LK_TW);
 }
 
-// ---------------------------------------------------------------- iteration tile
-// One Gauss-Newton iteration (Sect. 2.4) on one LK_TH x LK_TW output tile. Per pixel of
+// ----------------------------------------------------------- generic iteration tile
+// One Gauss-Newton iteration (Sect. 2.4) on one LK_TH x LK_TW output tile, for any
+// window radius r given at run time (the fixed-radius tile below is the fast path). Per pixel of
 // the tile plus an r-pixel halo: warp I2 by the current estimate, take the gradient of
 // I2 there, form e~ = I1 - I2w + g.(u - u_ref) and the five products; then box sums
 // (rows, then columns) and the 2x2 solve for the new estimate u_ref + x.
 // u_ref is the estimate at the tile centre: the equations are exact for any constant
 // reference, and subtracting one keeps the FP32 right-hand side small.
 template <typename T, bool NC>
-__device__ __forceinline__ void lk_tile(const IterArgs &a, int tile, int r, float fp64_cond, float *smem)
+__device__ __forceinline__ void lk_tile_generic(const IterArgs &a, int tile, int r, float fp64_cond, float *smem)
 {
     const int RH = LK_TH + 2 * r, RW = LK_TW + 2 * r;
     const int plane = RH * RW;
@@ -272,6 +276,366 @@ __device__ __forceinline__ void lk_tile(const IterArgs &a, int tile, int r, floa
             a.v_out[(size_t)y * a.W + x] = f.y;
         }
     }
+}
+
+
+// ------------------------------------------------------- fixed-radius iteration tile
+// The same iteration with the window radius R known at compile time (R >= 2). Box
+// sums are formed for groups of 4 consecutive outputs at once: the 2R-2 terms in the
+// middle of the 4 windows are added once and shared, each output adds its own 3 edge
+// terms (4.25 additions per output and channel for R = 4, instead of 8). Groups start
+// at multiples of 4 in image coordinates (tiles are multiples of 4 wide and high), so
+// the order of the additions depends only on the pixel's position, not on the tiling:
+// the batched and the per-pair launches give the same bits.
+template <int R> struct FixedTile {
+    static_assert(R >= 2, "the grouped box sums need 2R >= 4");
+    static constexpr int W = 2 * R + 1;                // window width
+    static constexpr int NV4 = (2 * R + 4 + 3) / 4;    // float4 loads for 4 outputs' windows
+    static constexpr int RH = LK_TH + 2 * R;           // region rows (tile + halo)
+    static constexpr int RW = LK_TW + 2 * R;           // region columns
+    static constexpr int RWP = LK_TW + 4 * NV4 - 4;    // padded row length (>= RW, multiple of 4)
+    static constexpr int PLANE = RH * RWP;
+    static constexpr int NREG = RH * RW;               // region pixels
+    static constexpr int PER = (NREG + LK_THREADS - 1) / LK_THREADS;   // region pixels per thread
+    // I2 staged in shared memory as FP32: the bounding box of every tap the region's
+    // warps read, when it holds at most FBOX floats (else the taps come from global).
+    static constexpr int FBOX = (RW + 10) * (RH + 10);
+    static constexpr int OFF_FBOX = 5 * PLANE;
+    static constexpr int OFF_BAR = (OFF_FBOX + FBOX + 1) / 2 * 2;   // 8-byte aligned mbarrier
+    static constexpr int OFF_BOX = OFF_BAR + 2;                      // 4 ints: box bounds
+    static constexpr int SMEM_FLOATS = OFF_BOX + 4;
+    static constexpr int MIN_BLOCKS = R <= 6 ? 3 : 2;
+};
+
+constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's row copies
+
+// Bilinear sample from the staged FP32 box (rows by0.., columns bx0.., row length bw),
+// with the same clamping as bil().
+__device__ __forceinline__ float bil_box(const float *box, int bw, int bx0, int by0, int H, int W, float x, float y)
+{
+    x = fminf(fmaxf(x, 0.0f), (float)(W - 1));
+    y = fminf(fmaxf(y, 0.0f), (float)(H - 1));
+    const float fx = floorf(x), fy = floorf(y);
+    const int x0 = (int)fx, y0 = (int)fy;
+    const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
+    const float ax = x - fx, ay = y - fy;
+    const float *r0 = box + (y0 - by0) * bw - bx0, *r1 = box + (y1 - by0) * bw - bx0;
+    return lerpf(lerpf(r0[x0], r0[x1], ax), lerpf(r1[x0], r1[x1], ax), ay);
+}
+
+// sample_grad() with the taps read from the staged box.
+__device__ __forceinline__ void sample_grad_box(const float *box, int bw, int bx0, int by0, int H, int W, float px,
+                                                float py, float &Iw, float &gx, float &gy)
+{
+    if (px >= 1.0f && py >= 1.0f && px < (float)(W - 2) && py < (float)(H - 2)) {
+        const float fx = floorf(px), fy = floorf(py);
+        const int x0 = (int)fx, y0 = (int)fy;
+        const float ax = px - fx, ay = py - fy;
+        const float *rm = box + (y0 - 1 - by0) * bw + (x0 - bx0);
+        const float *r0 = rm + bw, *r1 = r0 + bw, *r2 = r1 + bw;
+        const float a0 = rm[0], a1 = rm[1];
+        const float bm = r0[-1], b0 = r0[0], b1 = r0[1], b2 = r0[2];
+        const float cm = r1[-1], c0 = r1[0], c1 = r1[1], c2 = r1[2];
+        const float d0 = r2[0], d1 = r2[1];
+        const float top = lerpf(b0, b1, ax), bot = lerpf(c0, c1, ax);
+        Iw = lerpf(top, bot, ay);
+        gx = (lerpf(lerpf(b1, b2, ax), lerpf(c1, c2, ax), ay) - lerpf(lerpf(bm, b0, ax), lerpf(cm, c0, ax), ay)) * 0.5f;
+        gy = (lerpf(bot, lerpf(d0, d1, ax), ay) - lerpf(lerpf(a0, a1, ax), top, ay)) * 0.5f;
+    } else {
+        Iw = bil_box(box, bw, bx0, by0, H, W, px, py);
+        gx = (bil_box(box, bw, bx0, by0, H, W, px + 1.0f, py) - bil_box(box, bw, bx0, by0, H, W, px - 1.0f, py)) * 0.5f;
+        gy = (bil_box(box, bw, bx0, by0, H, W, px, py + 1.0f) - bil_box(box, bw, bx0, by0, H, W, px, py - 1.0f)) * 0.5f;
+    }
+}
+
+template <typename T> __device__ __forceinline__ float ld_smem_elem(const unsigned char *p)
+{
+    return ldf<false>(reinterpret_cast<const T *>(p));
+}
+
+// o[j] = sum_{k=0}^{2R} v[j+k], j = 0..3, from v[0 .. 2R+3].
+template <int R>
+__device__ __forceinline__ void box4(const float *v, float o[4])
+{
+    float m = v[3];
+#pragma unroll
+    for (int k = 4; k <= 2 * R; ++k) m += v[k];
+    o[0] = ((v[0] + v[1]) + v[2]) + m;
+    o[1] = ((v[1] + v[2]) + m) + v[2 * R + 1];
+    o[2] = ((v[2] + m) + v[2 * R + 1]) + v[2 * R + 2];
+    o[3] = ((m + v[2 * R + 1]) + v[2 * R + 2]) + v[2 * R + 3];
+}
+
+// Horizontal pass, in place: row ry of plane c becomes, at columns 0..LK_TW-1, the
+// window sums of the outputs of that row.
+template <int R>
+__device__ __forceinline__ void box_h_inplace(float *P)
+{
+    using F = FixedTile<R>;
+    constexpr int NG = LK_TW / 4;
+    constexpr int NITEMS = F::RH * NG;
+    constexpr int IT = (NITEMS + LK_THREADS - 1) / LK_THREADS;
+#pragma unroll 1
+    for (int c = 0; c < 5; ++c) {
+        float *Pc = P + c * F::PLANE;
+        float4 res[IT];
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+            const int i = threadIdx.x + k * LK_THREADS;
+            if (i < NITEMS) {
+                const int ry = i / NG, g = i % NG;
+                const float4 *src = reinterpret_cast<const float4 *>(Pc + ry * F::RWP + 4 * g);
+                float v[4 * F::NV4];
+#pragma unroll
+                for (int q = 0; q < F::NV4; ++q) {
+                    const float4 t = src[q];
+                    v[4 * q] = t.x;
+                    v[4 * q + 1] = t.y;
+                    v[4 * q + 2] = t.z;
+                    v[4 * q + 3] = t.w;
+                }
+                float o[4];
+                box4<R>(v, o);
+                res[k] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+        __syncthreads();   // every read of plane c is done before it is overwritten
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+            const int i = threadIdx.x + k * LK_THREADS;
+            if (i < NITEMS) {
+                const int ry = i / NG, g = i % NG;
+                *reinterpret_cast<float4 *>(Pc + ry * F::RWP + 4 * g) = res[k];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Vertical pass for the 4 outputs (rows 4g..4g+3, column tx) of every channel.
+template <int R>
+__device__ __forceinline__ void box_v4(const float *P, int g, int tx, float s[5][4])
+{
+    using F = FixedTile<R>;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        const float *col = P + c * F::PLANE + 4 * g * F::RWP + tx;
+        float v[2 * R + 4];
+#pragma unroll
+        for (int q = 0; q < 2 * R + 4; ++q) v[q] = col[q * F::RWP];
+        box4<R>(v, s[c]);
+    }
+}
+
+// The tile's mbarrier: initialised once per block, before the first tile.
+template <int R> __device__ __forceinline__ void lk_tile_init(float *smem)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(reinterpret_cast<uint64_t *>(smem + FixedTile<R>::OFF_BAR), 1);
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+}
+
+// Returns false if the staging copy did not complete in time (then OF_ETIMEOUT is in
+// *a.status, nothing of the tile was written, and the block must stop).
+template <typename T, bool NC, int R>
+__device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float fp64_cond, float *smem,
+                                              uint32_t &phase)
+{
+    using F = FixedTile<R>;
+    float *P = smem;
+    float *fbox = smem + F::OFF_FBOX;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + F::OFF_BAR);
+    int *s_box = reinterpret_cast<int *>(smem + F::OFF_BOX);
+    const int tyi = tile / a.tiles_x;
+    const int ty0 = tyi * LK_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
+    const float2 ref = flow_at<NC>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + LK_TH / 2, a.H - 1));
+    const T *I1 = static_cast<const T *>(a.I1);
+    const T *I2 = static_cast<const T *>(a.I2);
+    if (threadIdx.x == 0) {
+        s_box[0] = INT_MAX;
+        s_box[1] = INT_MIN;
+        s_box[2] = INT_MAX;
+        s_box[3] = INT_MIN;
+    }
+    __syncthreads();   // the previous tile's readers of smem are done; s_box is reset
+    // pass 0: the bounding box of the I2 taps the region's pixels will read
+    int lx0 = INT_MAX, lx1 = INT_MIN, ly0 = INT_MAX, ly1 = INT_MIN;
+#pragma unroll 4
+    for (int i = threadIdx.x; a.stage_i2 && i < F::NREG; i += LK_THREADS) {
+        const int ry = i / F::RW, rx = i - ry * F::RW;
+        const int y = ty0 - R + ry, x = tx0 - R + rx;
+        if ((unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W) {
+            const float2 f = flow_at<NC>(a, x, y);
+            const int ix = (int)fminf(fmaxf((float)x + f.x, 0.0f), (float)(a.W - 1));
+            const int iy = (int)fminf(fmaxf((float)y + f.y, 0.0f), (float)(a.H - 1));
+            lx0 = min(lx0, ix - 1);
+            lx1 = max(lx1, ix + 2);
+            ly0 = min(ly0, iy - 1);
+            ly1 = max(ly1, iy + 2);
+        }
+    }
+    lx0 = __reduce_min_sync(0xffffffffu, lx0);
+    lx1 = __reduce_max_sync(0xffffffffu, lx1);
+    ly0 = __reduce_min_sync(0xffffffffu, ly0);
+    ly1 = __reduce_max_sync(0xffffffffu, ly1);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&s_box[0], lx0);
+        atomicMax(&s_box[1], lx1);
+        atomicMin(&s_box[2], ly0);
+        atomicMax(&s_box[3], ly1);
+    }
+    __syncthreads();
+    const int bx0 = max(s_box[0], 0), bx1 = min(s_box[1], a.W - 1);
+    const int by0 = max(s_box[2], 0), by1 = min(s_box[3], a.H - 1);
+    const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
+    constexpr int E = 16 / (int)sizeof(T);   // elements per 16-byte chunk
+    const int cx0 = bx0 / E, cx1 = bx1 / E;
+    const int rowbytes = (cx1 - cx0 + 1) * 16;
+    const bool staged = a.stage_i2 && bw > 0 && bh > 0 && bw * bh <= F::FBOX && bh * rowbytes <= 5 * F::PLANE * 4;
+    if (staged) {
+        // one round of row copies into the start of the (not yet written) product planes
+        unsigned char *raw = reinterpret_cast<unsigned char *>(P);
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, (uint32_t)(bh * rowbytes));
+            }
+            __syncwarp();
+            fence_proxy_async_global();
+            for (int k = threadIdx.x; k < bh; k += 32)
+                bulk_g2s(raw + k * rowbytes, I2 + (size_t)(by0 + k) * a.pitch + (size_t)cx0 * E, (uint32_t)rowbytes, bar);
+        }
+        const bool done = mbar_wait_bounded(bar, phase, STAGE_TIMEOUT_NS);
+        phase ^= 1u;
+        if (__syncthreads_or(!done)) {
+            if (threadIdx.x == 0 && a.status) atomicExch(a.status, DEV_TIMEOUT);
+            return false;
+        }
+        // convert the box to FP32
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int skip = (bx0 - cx0 * E) * (int)sizeof(T);
+        for (int r = warp; r < bh; r += LK_THREADS / 32) {
+            const unsigned char *src = raw + r * rowbytes + skip;
+            float *dst = fbox + r * bw;
+            for (int c = lane; c < bw; c += 32) dst[c] = ld_smem_elem<T>(src + c * (int)sizeof(T));
+        }
+        __syncthreads();   // the raw copy is consumed before the product planes are written
+    }
+    // stage 1: products over the tile and its R-pixel halo. The current estimates of
+    // S1 pixels are loaded before any of them is used, so that their latencies overlap.
+    constexpr int S1 = 4;
+#pragma unroll 1
+    for (int k0 = 0; k0 < F::PER; k0 += S1) {
+        float2 f[S1];
+        bool in[S1];
+#pragma unroll
+        for (int u = 0; u < S1; ++u) {
+            const int i = threadIdx.x + (k0 + u) * LK_THREADS;
+            const int ry = i / F::RW, rx = i - ry * F::RW;
+            const int y = ty0 - R + ry, x = tx0 - R + rx;
+            in[u] = i < F::NREG && (unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W;
+            f[u] = in[u] ? flow_at<NC>(a, x, y) : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < S1; ++u) {
+            const int i = threadIdx.x + (k0 + u) * LK_THREADS;
+            if (i >= F::NREG) break;
+            const int ry = i / F::RW, rx = i - ry * F::RW;
+            const int y = ty0 - R + ry, x = tx0 - R + rx;
+            float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f, p4 = 0.0f;
+            if (in[u]) {
+                float Iw, gx, gy;
+                if (staged)
+                    sample_grad_box(fbox, bw, bx0, by0, a.H, a.W, (float)x + f[u].x, (float)y + f[u].y, Iw, gx, gy);
+                else
+                    sample_grad<NC>(I2, a.pitch, a.H, a.W, (float)x + f[u].x, (float)y + f[u].y, Iw, gx, gy);
+                const float e =
+                    ldf<NC>(I1 + (size_t)y * a.pitch + x) - Iw + gx * (f[u].x - ref.x) + gy * (f[u].y - ref.y);
+                p0 = gx * gx;
+                p1 = gx * gy;
+                p2 = gy * gy;
+                p3 = gx * e;
+                p4 = gy * e;
+            }
+            float *q = P + ry * F::RWP + rx;
+            q[0] = p0;
+            q[F::PLANE] = p1;
+            q[2 * F::PLANE] = p2;
+            q[3 * F::PLANE] = p3;
+            q[4 * F::PLANE] = p4;
+        }
+    }
+    __syncthreads();
+    box_h_inplace<R>(P);
+    // vertical sums, solve and write, 4 rows of one column per item
+    constexpr int VITEMS = LK_TW * (LK_TH / 4);
+#pragma unroll 1
+    for (int i = threadIdx.x; i < VITEMS; i += LK_THREADS) {
+        const int tx = i % LK_TW, g = i / LK_TW;
+        const int x = tx0 + tx;
+        if (x >= a.W || ty0 + 4 * g >= a.H) continue;
+        float s[5][4];
+        box_v4<R>(P, g, tx, s);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int y = ty0 + 4 * g + j;
+            if (y >= a.H) break;
+            const float sj[5] = {s[0][j], s[1][j], s[2][j], s[3][j], s[4][j]};
+            float2 f = flow_at<NC>(a, x, y);
+            float xu, xv;
+            if (solve2(sj, fp64_cond, xu, xv)) f = make_float2(ref.x + xu, ref.y + xv);
+            if (a.fout) {
+                a.fout[(size_t)y * a.fout_pitch + x] = f;
+            } else {
+                a.u_out[(size_t)y * a.W + x] = f.x;
+                a.v_out[(size_t)y * a.W + x] = f.y;
+            }
+        }
+    }
+    return true;
+}
+
+// The iteration tile for radius R (0 = generic, radius r at run time). Returns false
+// when the block must stop (a staging copy timed out; recorded in *a.status).
+template <typename T, bool NC, int R>
+__device__ __forceinline__ bool lk_tile(const IterArgs &a, int tile, int r, float fp64_cond, float *smem,
+                                        uint32_t &phase)
+{
+    if constexpr (R == 0) {
+        lk_tile_generic<T, NC>(a, tile, r, fp64_cond, smem);
+        return true;
+    } else {
+        return lk_tile_fixed<T, NC, R>(a, tile, fp64_cond, smem, phase);
+    }
+}
+
+template <int R> __device__ __forceinline__ void lk_tile_prepare(float *smem)
+{
+    if constexpr (R != 0) lk_tile_init<R>(smem);
+}
+
+template <int R> constexpr int lk_min_blocks()
+{
+    if constexpr (R == 0) return 2;
+    else return FixedTile<R>::MIN_BLOCKS;
+}
+
+#ifndef OF_BATCH_MIN_BLOCKS
+#define OF_BATCH_MIN_BLOCKS 3
+#endif
+// Resident blocks per SM the persistent kernel is compiled for (its register cap).
+template <int R> constexpr int batch_min_blocks()
+{
+    constexpr int m = lk_min_blocks<R>();
+    return m < OF_BATCH_MIN_BLOCKS ? m : OF_BATCH_MIN_BLOCKS;
+}
+
+template <int R> inline __host__ __device__ int lk_tile_smem_floats(int r)
+{
+    if constexpr (R == 0) return lk_smem_floats(r);
+    else return FixedTile<R>::SMEM_FLOATS;
 }
 
 }  // namespace of

@@ -1,0 +1,150 @@
+// Kernels and launchers for one window radius. Each radius_<R>.cu defines OF_RADIUS
+// and includes this file; radius 0 is the generic kernel (radius given at run time).
+#pragma once
+
+#include "batch_device.cuh"
+#include "of_internal.cuh"
+#include "of_kernels.cuh"
+
+#ifndef OF_RADIUS
+#error "define OF_RADIUS before including radius_impl.cuh"
+#endif
+
+namespace of {
+
+template <typename T, int R>
+__global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>()) lk_iter_kernel(IterArgs a, int r, float fp64_cond)
+{
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    uint32_t phase = 0;
+    lk_tile_prepare<R>(smem);
+    lk_tile<T, true, R>(a, blockIdx.x, r, fp64_cond, smem, phase);
+}
+
+// The window sums of five given planes, through the same passes as the iteration tile.
+template <int R>
+__global__ void __launch_bounds__(LK_THREADS)
+window_sums_kernel(const float *ch, int H, int W, int r, int tiles_x, float *out)
+{
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    const int tile = blockIdx.x;
+    const int ty0 = (tile / tiles_x) * LK_TH, tx0 = (tile % tiles_x) * LK_TW;
+    const size_t N = (size_t)H * W;
+    if constexpr (R == 0) {
+        const int RH = LK_TH + 2 * r, RW = LK_TW + 2 * r;
+        const int plane = RH * RW;
+        float *P = smem, *S = smem + 5 * plane;
+        for (int i = threadIdx.x; i < plane; i += blockDim.x) {
+            const int ry = i / RW, rx = i - ry * RW;
+            const int y = ty0 - r + ry, x = tx0 - r + rx;
+            const bool in = y >= 0 && y < H && x >= 0 && x < W;
+            for (int c = 0; c < 5; ++c) P[c * plane + i] = in ? ch[c * N + (size_t)y * W + x] : 0.0f;
+        }
+        __syncthreads();
+        box_hsum(P, S, RH, RW, r);
+        __syncthreads();
+        for (int i = threadIdx.x; i < LK_TH * LK_TW; i += blockDim.x) {
+            const int ty = i / LK_TW, tx = i % LK_TW;
+            const int y = ty0 + ty, x = tx0 + tx;
+            if (y >= H || x >= W) continue;
+            float s[5];
+            box_vsum(S, RH, r, ty, tx, s);
+            for (int c = 0; c < 5; ++c) out[c * N + (size_t)y * W + x] = s[c];
+        }
+    } else {
+        using F = FixedTile<R>;
+        float *P = smem;
+        for (int i = threadIdx.x; i < F::RH * F::RW; i += blockDim.x) {
+            const int ry = i / F::RW, rx = i - ry * F::RW;
+            const int y = ty0 - R + ry, x = tx0 - R + rx;
+            const bool in = y >= 0 && y < H && x >= 0 && x < W;
+            for (int c = 0; c < 5; ++c) P[c * F::PLANE + ry * F::RWP + rx] = in ? ch[c * N + (size_t)y * W + x] : 0.0f;
+        }
+        __syncthreads();
+        box_h_inplace<R>(P);
+        for (int i = threadIdx.x; i < LK_TW * (LK_TH / 4); i += blockDim.x) {
+            const int tx = i % LK_TW, g = i / LK_TW;
+            const int x = tx0 + tx;
+            if (x >= W) continue;
+            float s[5][4];
+            box_v4<R>(P, g, tx, s);
+            for (int j = 0; j < 4; ++j) {
+                const int y = ty0 + 4 * g + j;
+                if (y >= H) break;
+                for (int c = 0; c < 5; ++c) out[c * N + (size_t)y * W + x] = s[c][j];
+            }
+        }
+    }
+}
+
+template <int R> size_t radius_smem_bytes(int r)
+{
+    const size_t lk = sizeof(float) * (size_t)lk_tile_smem_floats<R>(r);
+    const size_t pyr = sizeof(float) * (size_t)PYR_SMEM_FLOATS;
+    return lk > pyr ? lk : pyr;
+}
+
+template <typename T, int R> static cudaError_t lk_for(const IterArgs &a, int r, float fp64_cond, cudaStream_t s)
+{
+    lk_iter_kernel<T, R><<<a.tiles, LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r), s>>>(a, r, fp64_cond);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s)
+{
+    switch (elem) {
+    case ET_U8: return lk_for<uint8_t, R>(a, r, fp64_cond, s);
+    case ET_U16: return lk_for<uint16_t, R>(a, r, fp64_cond, s);
+    case ET_F32: return lk_for<float, R>(a, r, fp64_cond, s);
+    case ET_F16: return lk_for<__half, R>(a, r, fp64_cond, s);
+    default: return lk_for<__nv_bfloat16, R>(a, r, fp64_cond, s);
+    }
+}
+
+template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, float *out, cudaStream_t s)
+{
+    const int tiles_x = (W + LK_TW - 1) / LK_TW, tiles_y = (H + LK_TH - 1) / LK_TH;
+    window_sums_kernel<R><<<tiles_x * tiles_y, LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r), s>>>(
+        ch, H, W, r, tiles_x, out);
+    return cudaGetLastError();
+}
+
+template <int R> void *batch_kernel_ptr(int in_format, int storage)
+{
+    if (in_format == OF_U8) {
+        if (storage == OF_F32) return (void *)batch_kernel<uint8_t, float, R>;
+        if (storage == OF_F16) return (void *)batch_kernel<uint8_t, __half, R>;
+        return (void *)batch_kernel<uint8_t, __nv_bfloat16, R>;
+    }
+    if (storage == OF_F32) return (void *)batch_kernel<uint16_t, float, R>;
+    if (storage == OF_F16) return (void *)batch_kernel<uint16_t, __half, R>;
+    return (void *)batch_kernel<uint16_t, __nv_bfloat16, R>;
+}
+
+// Raise the dynamic shared memory limit of this radius's kernels on the current device.
+template <int R> cudaError_t radius_configure()
+{
+    const int bytes = (int)radius_smem_bytes<R>(R == 0 ? MAX_RADIUS : R);
+    cudaError_t e;
+#define OF_SET(fn) if ((e = cudaFuncSetAttribute((const void *)(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e
+    OF_SET((lk_iter_kernel<uint8_t, R>));
+    OF_SET((lk_iter_kernel<uint16_t, R>));
+    OF_SET((lk_iter_kernel<float, R>));
+    OF_SET((lk_iter_kernel<__half, R>));
+    OF_SET((lk_iter_kernel<__nv_bfloat16, R>));
+    OF_SET((window_sums_kernel<R>));
+    for (int f = 0; f < 2; ++f)
+        for (int st = 0; st < 3; ++st) OF_SET(batch_kernel_ptr<R>(f, st));
+#undef OF_SET
+    return cudaSuccess;
+}
+
+template cudaError_t lk_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
+template cudaError_t ws_launch<OF_RADIUS>(const float *, int, int, int, float *, cudaStream_t);
+template void *batch_kernel_ptr<OF_RADIUS>(int, int);
+template cudaError_t radius_configure<OF_RADIUS>();
+template size_t radius_smem_bytes<OF_RADIUS>(int);
+
+}  // namespace of

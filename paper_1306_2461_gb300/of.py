@@ -19,6 +19,7 @@ OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_EDEVICE, OF_ETIMEOUT, OF_ESTATE, OF_EB
 OF_U8, OF_U16 = 0, 1
 OF_F32, OF_F16, OF_BF16 = 0, 1, 2
 OF_FLAG_NO_GRAPH = 0x1
+OF_FLAG_STAGE_I2 = 0x2
 STORAGE = {"f32": OF_F32, "f16": OF_F16, "bf16": OF_BF16}
 
 

@@ -85,6 +85,22 @@ def test_mixed_size_batch_64_pairs(of, oracle_mod):
         f.close()
 
 
+def test_batch_staged_i2_equals_single(of):
+    import torch
+    pairs = synth.make_batch(5, seed=9, sizes=((160, 256), (256, 256), (96, 320)))
+    flows = [of.Flow(of.Plan.make(*p.shape, 3, 4, 4, bits=8, storage="f16", flags=of.OF_FLAG_STAGE_I2))
+             for p in pairs]
+    I1 = [to_dev(p.I1) for p in pairs]
+    I2 = [to_dev(p.I2) for p in pairs]
+    ub, vb = of.compute_batch(flows, I1, I2)
+    torch.cuda.synchronize()
+    for i, p in enumerate(pairs):
+        u1, v1 = single(of, of.Plan.make(*p.shape, 3, 4, 4, bits=8, storage="f16"), I1[i], I2[i])
+        assert torch.equal(ub[i], u1) and torch.equal(vb[i], v1), i
+    for f in flows:
+        f.close()
+
+
 def test_batch_with_reused_first_image(of):
     # scheme 1 inside a batch: half the pairs reuse their previous second image
     import torch

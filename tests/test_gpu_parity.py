@@ -200,3 +200,20 @@ def test_invalid_calls_are_rejected(of):
 
 def test_bounded_device_wait_times_out(of):
     assert of.debug_wait_timeout(2000) == of.OF_ETIMEOUT
+
+
+@pytest.mark.parametrize("storage,r", [("f16", 4), ("f32", 3), ("f16", 10), ("bf16", 5)])
+def test_staged_i2_equals_gathered(of, storage, r):
+    # staging the tile's I2 footprint in shared memory reads the same values and does
+    # the same arithmetic as gathering them from global memory: identical bits
+    import torch
+    p = synth.make_c2(320, 448, seed=4)
+    res = []
+    for flags in (0, of.OF_FLAG_STAGE_I2):
+        plan = of.Plan.make(320, 448, 3, r, 3, bits=12, storage=storage, flags=flags)
+        with of.Flow(plan) as f:
+            u, v = f.compute(to_dev(p.I1), to_dev(p.I2))
+            torch.cuda.synchronize()
+            assert f.sync_status() == of.OF_OK
+            res.append((u.clone(), v.clone()))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
