@@ -403,7 +403,34 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
     out["e2e"] = {"value": B * Ke / (ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": B * 2 * H * W * 2,
                   "d2h_bytes_per_step": B * 2 * H * W * 4, "steps": Ke,
                   "path": "pinned host frames -> of_compute_batch -> pinned host u, v (one stream)"}
+    out["serving"] = serving_leg(torch, synth)
     return out
+
+
+def serving_leg(torch, synth, rate_per_stream=125.0, warmup_s=0.25, measure_s=2.0, frames_per_stream=3):
+    """16 camera streams (8 x 512^2, 6 x 1024^2, 2 x 2048^2, 12-bit), Poisson arrivals
+    totalling 2000 frames/s, open loop; each stream's previous pyramid stays resident.
+    Latency = completion seen by the server's worker - scheduled arrival (includes the
+    host-to-device copy of the frame; no device-to-host copy of the field)."""
+    from paper_1306_2461_gb300 import serve
+    streams_cfg = synth.serving_streams(seed=4)
+    with serve.Server(levels=LEVELS, radius=RADIUS, iterations=ITERS, bits=BITS, storage="f16",
+                      hbm_budget_bytes=64 << 30, max_batch=64, max_inflight=2) as srv:
+        streams = []
+        for ps in streams_cfg:
+            frames = []
+            for _ in range(frames_per_stream):
+                frames.append(serve.pinned_frame(ps.frame()))
+                ps.advance()
+            streams.append((srv.open_stream(ps.H, ps.W), frames))
+        arrivals = synth.poisson_arrivals(len(streams), rate_per_stream, warmup_s + measure_s, seed=4)
+        results, _ = serve.run_open_loop(srv, streams, arrivals, warmup_s=warmup_s)
+        summ = serve.summarize(results, measure_s)
+        st = srv.stats()
+    summ.update({"streams": "8x512^2 + 6x1024^2 + 2x2048^2, 12-bit", "offered_frames_per_s": rate_per_stream * 16,
+                 "window_s": measure_s, "ticks": st["ticks"],
+                 "note": f"{frames_per_stream} rendered frames per stream, cycled; latency from scheduled arrival"})
+    return summ
 
 
 if __name__ == "__main__":

@@ -181,6 +181,88 @@ int of_window_sums(const float *ch, int32_t H, int32_t W, int32_t r, float *out,
  * until it returns and reports OF_ETIMEOUT (the expected outcome) or OF_ECUDA. */
 int of_debug_wait_timeout(int32_t timeout_us);
 
+/* ------------------------------------------------------------------------------
+ * Serving: camera streams of mixed resolutions on one GPU, continuous batching.
+ *
+ * Each stream delivers frames in order; every frame after the first yields the field
+ * from the previous frame to it. The previous frame's pyramid stays resident on the
+ * device and is reused as the first image of the next pair (computing scheme 1 of
+ * Sect. 2.4), so each field processes one new image. Streams are admitted against an
+ * HBM budget. A worker thread packs the next pending frame of every stream into one
+ * persistent batched launch ("tick"); frames arriving while ticks run join the next
+ * tick as soon as fewer than max_inflight ticks are on the device, their host-to-
+ * device copies overlapping the running tick. All calls are thread-safe.
+ */
+typedef struct of_server *of_server_t;
+
+typedef struct of_server_config {
+    int32_t levels, radius, iterations; /* the method, as in of_plan, shared by all streams */
+    int32_t in_format, in_bits, storage;
+    float fp64_cond;
+    uint32_t flags;                     /* OF_FLAG_STAGE_I2 (OF_FLAG_NO_GRAPH is ignored) */
+    uint64_t hbm_budget_bytes;          /* device memory all open streams may hold together */
+    int32_t max_batch;                  /* pairs per tick, 1..4096 */
+    int32_t max_inflight;               /* ticks queued on the device at once, 1..8 */
+} of_server_config;
+
+/* One finished frame. Times are of_server_now_ns() values (host steady clock). */
+typedef struct of_result {
+    int32_t stream;      /* stream id */
+    int32_t status;      /* OF_OK or the error that affected this frame */
+    uint64_t tag;        /* the caller's tag from of_server_submit */
+    int64_t arrival_ns;  /* when the frame arrived (given to, or taken by, of_server_submit) */
+    int64_t launch_ns;   /* when its tick was queued on the device */
+    int64_t done_ns;     /* when the worker saw its tick complete */
+    int32_t batch;       /* pairs in that tick */
+    int32_t has_field;   /* 0 for a stream's first frame (staged only), 1 when u, v were written */
+} of_result;
+
+/* Defaults: 3 levels, r = 4, 5 iterations, 12-bit uint16 input, FP16 storage,
+ * fp64_cond 1e3, 8 GiB budget, max_batch 64, max_inflight 2. Host only. */
+void of_server_config_init(of_server_config *c);
+
+/* Create a server on the current device (streams, launch slots, worker thread).
+ * OF_EINVAL, OF_ENOMEM, OF_ECUDA. */
+int of_server_create(const of_server_config *c, of_server_t *out);
+
+/* Admit a stream of H x W frames: allocates its workspace (of_workspace_bytes of its
+ * plan) and two frame staging buffers. OF_ENOMEM if that would exceed the budget;
+ * *id receives the stream id (>= 0, reused after a close). */
+int of_server_open_stream(of_server_t s, int32_t H, int32_t W, int32_t *id);
+
+/* Close a stream whose submitted frames have all been taken into ticks: waits for
+ * those ticks, then frees its memory. OF_EBUSY if frames are still queued. */
+int of_server_close_stream(of_server_t s, int32_t id);
+
+/*
+ * Queue one frame of stream `id`.
+ *  frame: host memory (pinned for full copy speed), H*W elements of the input format;
+ *         it must stay valid and unchanged until this frame's result is reported.
+ *  u, v:  device, H*W floats each, receive the field from the stream's previous
+ *         frame to this one; may be NULL for the stream's first frame.
+ *  tag:   returned in the result. arrival_ns: the frame's arrival time (0 = now);
+ *         latency is measured from it, so late submissions are charged in full.
+ * OF_EINVAL, OF_EBUSY (256 frames already queued on this stream), or a sticky error.
+ */
+int of_server_submit(of_server_t s, int32_t id, const void *frame, float *u, float *v, uint64_t tag,
+                     int64_t arrival_ns);
+
+/* Move up to `max` finished results into out[0..*n), waiting up to timeout_us for the
+ * first one. Returns OF_OK or the server's sticky error. */
+int of_server_poll(of_server_t s, of_result *out, int32_t max, int32_t *n, int32_t timeout_us);
+
+/* Wait until every submitted frame is finished (OF_ETIMEOUT after timeout_ms). */
+int of_server_drain(of_server_t s, int32_t timeout_ms);
+
+/* Ticks launched, pairs computed, device bytes held by open streams. */
+int of_server_stats(of_server_t s, int64_t *ticks, int64_t *pairs, uint64_t *hbm_used);
+
+/* The clock of of_result times (nanoseconds, monotonic). */
+int64_t of_server_now_ns(void);
+
+/* Stop the worker, wait for the device, free everything. NULL is a no-op. */
+int of_server_destroy(of_server_t s);
+
 /* Static text for a status code. */
 const char *of_status_string(int status);
 

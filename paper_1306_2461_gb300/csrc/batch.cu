@@ -80,6 +80,8 @@ cudaError_t launch_direct(const BatchEntry &e, cudaStream_t st)
 
 using namespace of;
 
+namespace of {
+
 static bool same_method(const of_plan &a, const of_plan &b)
 {
     return a.levels == b.levels && a.radius == b.radius && a.iterations == b.iterations &&
@@ -87,10 +89,17 @@ static bool same_method(const of_plan &a, const of_plan &b)
            a.fp64_cond == b.fp64_cond && (a.flags & OF_FLAG_STAGE_I2) == (b.flags & OF_FLAG_STAGE_I2);
 }
 
-extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
-                                float *const *us, float *const *vs, of_stream_t stream)
+// The host image of one batch: descriptors, work-list prefix sums, slots, launch shape.
+struct BatchBuild {
+    std::vector<BatchPair> pairs;
+    std::vector<int32_t> prefix;
+    std::vector<int> s1, s2;
+    int nphases = 0, npyr = 0, max_items = 0;
+};
+
+static int build_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
+                       float *const *us, float *const *vs, BatchBuild &b)
 {
-    if (n == 0) return OF_OK;
     if (n < 0 || n > 65536 || !hs || !I1s || !I2s || !us || !vs) return OF_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!hs[i] || !I2s[i] || !us[i] || !vs[i]) return OF_EINVAL;
@@ -100,26 +109,26 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return OF_EINVAL;
     }
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const of_plan &p0 = hs[0]->plan;
-    const int L = p0.levels, npyr = L > 1 ? L - 1 : 1, nphases = npyr + L * p0.iterations;
-
-    // descriptors
-    std::vector<BatchPair> pairs(n);
-    std::vector<int32_t> prefix((size_t)nphases * (n + 1));
-    std::vector<int> s1(n), s2(n);
+    const int L = p0.levels;
+    b.npyr = L > 1 ? L - 1 : 1;
+    b.nphases = b.npyr + L * p0.iterations;
+    b.pairs.assign(n, BatchPair());
+    b.prefix.assign((size_t)b.nphases * (n + 1), 0);
+    b.s1.assign(n, 0);
+    b.s2.assign(n, 1);
     for (int i = 0; i < n; ++i) {
         of_ctx *h = hs[i];
-        s1[i] = I1s[i] ? 0 : h->prev_slot;
-        s2[i] = I1s[i] ? 1 : 1 - h->prev_slot;
-        BatchPair &bp = pairs[i];
+        b.s1[i] = I1s[i] ? 0 : h->prev_slot;
+        b.s2[i] = I1s[i] ? 1 : 1 - h->prev_slot;
+        BatchPair &bp = b.pairs[i];
         memset(&bp, 0, sizeof(bp));
         bp.raw[0] = I1s[i];
         bp.raw[1] = I2s[i];
         bp.u = us[i];
         bp.v = vs[i];
-        bp.pyr[0] = h->pyr[s1[i]];
-        bp.pyr[1] = h->pyr[s2[i]];
+        bp.pyr[0] = h->pyr[b.s1[i]];
+        bp.pyr[1] = h->pyr[b.s2[i]];
         bp.flow[0] = h->flow[0];
         bp.flow[1] = h->flow[1];
         bp.status = h->status;
@@ -131,31 +140,166 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
             bp.off[l] = h->lay.level_off[l];
         }
     }
-    int max_items = 0;
-    for (int ph = 0; ph < nphases; ++ph) {
-        int32_t *pre = &prefix[(size_t)ph * (n + 1)];
+    b.max_items = 0;
+    for (int ph = 0; ph < b.nphases; ++ph) {
+        int32_t *pre = &b.prefix[(size_t)ph * (n + 1)];
         pre[0] = 0;
         for (int i = 0; i < n; ++i) {
-            const BatchPair &bp = pairs[i];
+            const BatchPair &bp = b.pairs[i];
             int64_t cnt;
-            if (ph < npyr) {
+            if (ph < b.npyr) {
                 const int Ho = (bp.H[ph] + 1) / 2, Wo = (bp.W[ph] + 1) / 2;
                 cnt = (int64_t)((Wo + PYR_TW - 1) / PYR_TW) * ((Ho + PYR_TH - 1) / PYR_TH) * (2 - bp.first_image);
             } else {
-                const int l = L - 1 - (ph - npyr) / p0.iterations;
+                const int l = L - 1 - (ph - b.npyr) / p0.iterations;
                 cnt = (int64_t)((bp.W[l] + LK_TW - 1) / LK_TW) * ((bp.H[l] + LK_TH - 1) / LK_TH);
             }
             if (pre[i] + cnt > INT32_MAX) return OF_EINVAL;
             pre[i + 1] = (int32_t)(pre[i] + cnt);
         }
-        if (pre[n] > max_items) max_items = pre[n];
+        if (pre[n] > b.max_items) b.max_items = pre[n];
     }
-    const size_t pairs_bytes = sizeof(BatchPair) * n, prefix_bytes = sizeof(int32_t) * prefix.size();
+    return OF_OK;
+}
+
+static void fill_header(BatchHdr &hd, const of_plan &p0, const BatchBuild &b, char *dev, size_t bar_off)
+{
+    const size_t pairs_bytes = sizeof(BatchPair) * b.pairs.size();
+    hd.pairs = reinterpret_cast<const BatchPair *>(dev);
+    hd.prefix = reinterpret_cast<const int32_t *>(dev + pairs_bytes);
+    hd.barrier = reinterpret_cast<unsigned int *>(dev + bar_off);
+    hd.abort = reinterpret_cast<int *>(dev + bar_off + sizeof(unsigned int));
+    hd.npairs = (int32_t)b.pairs.size();
+    hd.levels = p0.levels;
+    hd.iterations = p0.iterations;
+    hd.radius = p0.radius;
+    hd.nphases = b.nphases;
+    hd.npyr = b.npyr;
+    hd.fp64_cond = p0.fp64_cond;
+    hd.timeout_ns = BARRIER_TIMEOUT_NS;
+    hd.stage_i2 = (p0.flags & OF_FLAG_STAGE_I2) ? 1 : 0;
+}
+
+static size_t bar_offset(const BatchBuild &b)
+{
+    return (sizeof(BatchPair) * b.pairs.size() + sizeof(int32_t) * b.prefix.size() + 255) / 256 * 256;
+}
+
+// Grid size of the persistent kernel: every block resident at once (cooperative).
+static int grid_for(void *fn, size_t smem, int device, int max_items, dim3 &grid)
+{
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LK_THREADS, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || per_sm < 1)
+        return OF_ECUDA;
+    int g = per_sm * sms;
+    if (g > max_items) g = max_items > 0 ? max_items : 1;
+    grid = dim3(g);
+    return OF_OK;
+}
+
+static int commit_state(int32_t n, const of_handle *hs, const BatchBuild &b, cudaStream_t st)
+{
+    for (int i = 0; i < n; ++i) {
+        of_ctx *h = hs[i];
+        h->prev_slot = b.s2[i];
+        h->has_prev = true;
+        h->last_s1 = b.s1[i];
+        h->last_s2 = b.s2[i];
+        h->computed = true;
+        if (cudaEventRecord(h->done, st) != cudaSuccess) return OF_ECUDA;
+    }
+    return OF_OK;
+}
+
+// ------------------------------------------------------------- reusable slots
+int batch_slot_init(BatchSlot &s, int max_pairs, int max_phases)
+{
+    s.max_pairs = max_pairs;
+    s.max_phases = max_phases;
+    const size_t bytes = (sizeof(BatchPair) * max_pairs + sizeof(int32_t) * (size_t)max_phases * (max_pairs + 1) +
+                          255) / 256 * 256;
+    s.desc_bytes = bytes;
+    if (cudaMalloc((void **)&s.dev, bytes + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return OF_ENOMEM;
+    }
+    if (cudaMallocHost((void **)&s.host, bytes) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        batch_slot_free(s);
+        return OF_ENOMEM;
+    }
+    return OF_OK;
+}
+
+void batch_slot_free(BatchSlot &s)
+{
+    if (s.done) cudaEventSynchronize(s.done);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.host) cudaFreeHost(s.host);
+    if (s.dev) cudaFree(s.dev);
+    s = BatchSlot();
+}
+
+// One persistent launch on `st` from a preallocated slot: the descriptors go through
+// the slot's pinned buffer with one asynchronous copy; no allocation, no graph. The
+// slot must not be in use by an unfinished launch (its `done` event).
+int batch_run_slot(BatchSlot &slot, int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
+                   float *const *us, float *const *vs, cudaStream_t st)
+{
+    if (n == 0) return OF_OK;
+    BatchBuild b;
+    int rc = build_batch(n, hs, I1s, I2s, us, vs, b);
+    if (rc) return rc;
+    if (n > slot.max_pairs || b.nphases > slot.max_phases) return OF_EINVAL;
+    const of_plan &p0 = hs[0]->plan;
+    const size_t pairs_bytes = sizeof(BatchPair) * n, prefix_bytes = sizeof(int32_t) * b.prefix.size();
+    const size_t bar_off = bar_offset(b);
+    memcpy(slot.host, b.pairs.data(), pairs_bytes);
+    memcpy(slot.host + pairs_bytes, b.prefix.data(), prefix_bytes);
+    BatchHdr hd;
+    fill_header(hd, p0, b, slot.dev, bar_off);
+    void *fn = batch_kernel_for(p0.in_format, p0.storage, p0.radius);
+    const size_t smem = batch_smem_bytes(p0.radius);
+    dim3 grid;
+    if ((rc = grid_for(fn, smem, hs[0]->device, b.max_items, grid))) return rc;
+    if (cudaMemcpyAsync(slot.dev, slot.host, pairs_bytes + prefix_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(hd.barrier, 0, 2 * sizeof(unsigned int), st) != cudaSuccess)
+        return OF_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(LK_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {(void *)&hd};
+    if (cudaLaunchKernelExC(&cfg, fn, args) != cudaSuccess || cudaEventRecord(slot.done, st) != cudaSuccess)
+        return OF_ECUDA;
+    return commit_state(n, hs, b, st);
+}
+
+}  // namespace of
+
+extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
+                                float *const *us, float *const *vs, of_stream_t stream)
+{
+    if (n == 0) return OF_OK;
+    BatchBuild b;
+    int rc = build_batch(n, hs, I1s, I2s, us, vs, b);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const of_plan &p0 = hs[0]->plan;
+    const size_t pairs_bytes = sizeof(BatchPair) * n, prefix_bytes = sizeof(int32_t) * b.prefix.size();
     std::vector<char> key(pairs_bytes + prefix_bytes + sizeof(st) + 3 * sizeof(int));
     {
         char *k = key.data();
-        memcpy(k, pairs.data(), pairs_bytes);
-        memcpy(k + pairs_bytes, prefix.data(), prefix_bytes);
+        memcpy(k, b.pairs.data(), pairs_bytes);
+        memcpy(k + pairs_bytes, b.prefix.data(), prefix_bytes);
         memcpy(k + pairs_bytes + prefix_bytes, &st, sizeof(st));
         const int extra[3] = {p0.radius, p0.iterations * 2 + ((p0.flags & OF_FLAG_STAGE_I2) ? 1 : 0), hs[0]->device};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
@@ -176,44 +320,26 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
         BatchEntry &ne = *slot;
         ne.key = key;
         ne.device = hs[0]->device;
-        const size_t bar_off = (pairs_bytes + prefix_bytes + 255) / 256 * 256;
+        const size_t bar_off = bar_offset(b);
         cudaError_t err = cudaMalloc((void **)&ne.dev, bar_off + 256);
         if (err != cudaSuccess) {
             cudaGetLastError();
             ne = BatchEntry();
             return err == cudaErrorMemoryAllocation ? OF_ENOMEM : OF_ECUDA;
         }
-        if (cudaMemcpy(ne.dev, pairs.data(), pairs_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(ne.dev + pairs_bytes, prefix.data(), prefix_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        if (cudaMemcpy(ne.dev, b.pairs.data(), pairs_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ne.dev + pairs_bytes, b.prefix.data(), prefix_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaEventCreateWithFlags(&ne.done, cudaEventDisableTiming) != cudaSuccess) {
             release(ne);
             return OF_ECUDA;
         }
-        BatchHdr &hd = ne.hdr;
-        hd.pairs = reinterpret_cast<const BatchPair *>(ne.dev);
-        hd.prefix = reinterpret_cast<const int32_t *>(ne.dev + pairs_bytes);
-        hd.barrier = reinterpret_cast<unsigned int *>(ne.dev + bar_off);
-        hd.abort = reinterpret_cast<int *>(ne.dev + bar_off + sizeof(unsigned int));
-        hd.npairs = n;
-        hd.levels = L;
-        hd.iterations = p0.iterations;
-        hd.radius = p0.radius;
-        hd.nphases = nphases;
-        hd.npyr = npyr;
-        hd.fp64_cond = p0.fp64_cond;
-        hd.timeout_ns = BARRIER_TIMEOUT_NS;
-        hd.stage_i2 = (p0.flags & OF_FLAG_STAGE_I2) ? 1 : 0;
+        fill_header(ne.hdr, p0, b, ne.dev, bar_off);
         ne.fn = batch_kernel_for(p0.in_format, p0.storage, p0.radius);
         ne.smem = batch_smem_bytes(p0.radius);
-        int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ne.fn, LK_THREADS, ne.smem) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ne.device) != cudaSuccess || per_sm < 1) {
+        if ((rc = grid_for(ne.fn, ne.smem, ne.device, b.max_items, ne.grid))) {
             release(ne);
-            return OF_ECUDA;
+            return rc;
         }
-        int grid = per_sm * sms;
-        if (grid > max_items) grid = max_items > 0 ? max_items : 1;
-        ne.grid = dim3(grid);
         // capture [reset barrier, persistent kernel] as a graph when the stream allows it
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         const bool graphs = st != nullptr && !(p0.flags & OF_FLAG_NO_GRAPH) &&
@@ -236,14 +362,5 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
     cudaError_t err = e->exec ? cudaGraphLaunch(e->exec, st) : launch_direct(*e, st);
     if (err != cudaSuccess) return OF_ECUDA;
     if (cudaEventRecord(e->done, st) != cudaSuccess) return OF_ECUDA;
-    for (int i = 0; i < n; ++i) {
-        of_ctx *h = hs[i];
-        h->prev_slot = s2[i];
-        h->has_prev = true;
-        h->last_s1 = s1[i];
-        h->last_s2 = s2[i];
-        h->computed = true;
-        if (cudaEventRecord(h->done, st) != cudaSuccess) return OF_ECUDA;
-    }
-    return OF_OK;
+    return commit_state(n, hs, b, st);
 }

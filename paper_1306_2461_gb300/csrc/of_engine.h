@@ -61,4 +61,18 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
 int run_pair(of_ctx *h, const void *I1, const void *I2, float *u, float *v, int s1, int s2, cudaStream_t st);
 void drop_graphs(of_ctx *h);
 
+// A reusable launch slot for the persistent batch kernel: device and pinned host
+// buffers for the descriptors of up to max_pairs pairs and max_phases phases.
+struct BatchSlot {
+    char *dev = nullptr;
+    char *host = nullptr;
+    size_t desc_bytes = 0;
+    int max_pairs = 0, max_phases = 0;
+    cudaEvent_t done = nullptr;
+};
+int batch_slot_init(BatchSlot &s, int max_pairs, int max_phases);
+void batch_slot_free(BatchSlot &s);
+int batch_run_slot(BatchSlot &slot, int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
+                   float *const *us, float *const *vs, cudaStream_t st);
+
 }  // namespace of
