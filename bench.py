@@ -153,6 +153,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(local_ms, local_fields, world):
+    """Replicas (fields are independent): every rank timed its own batch; the job's time
+    is the slowest rank's and its fields are all ranks' together. Returns (ms, fields)."""
+    if world <= 1:
+        return float(local_ms), float(local_fields)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    f = torch.tensor([float(local_fields)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(f.item())
+
+
 def percentile(xs, q):
     return float(np.percentile(np.asarray(xs, np.float64), q)) if xs else None
 
@@ -279,12 +294,7 @@ def main():
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = ev[0][0].elapsed_time(ev[-1][1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    fields = B * args.steps * world
+    total_ms, fields = aggregate(ev[0][0].elapsed_time(ev[-1][1]), B * args.steps, world)
     value = fields / (total_ms / 1000.0)
 
     extras = {}

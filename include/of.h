@@ -263,6 +263,11 @@ int64_t of_server_now_ns(void);
 /* Stop the worker, wait for the device, free everything. NULL is a no-op. */
 int of_server_destroy(of_server_t s);
 
+/* Test hook for failure handling: the library's next n device allocations (of_create,
+ * of_server_open_stream, of_server_create) fail as if the device were out of memory.
+ * n = 0 clears it. Returns the previous count. Host only. */
+int of_debug_fail_allocs(int32_t n);
+
 /* Static text for a status code. */
 const char *of_status_string(int status);
 

@@ -220,7 +220,7 @@ int batch_slot_init(BatchSlot &s, int max_pairs, int max_phases)
     const size_t bytes = (sizeof(BatchPair) * max_pairs + sizeof(int32_t) * (size_t)max_phases * (max_pairs + 1) +
                           255) / 256 * 256;
     s.desc_bytes = bytes;
-    if (cudaMalloc((void **)&s.dev, bytes + 256) != cudaSuccess) {
+    if (dev_malloc((void **)&s.dev, bytes + 256) != cudaSuccess) {
         cudaGetLastError();
         return OF_ENOMEM;
     }

@@ -53,12 +53,12 @@ __device__ __forceinline__ bool bounded_wait_ge(const volatile unsigned int *wor
                                 long long timeout_ns)
 {
     const unsigned long long t0 = gtimer();
-    const long long cap = timeout_ns / 32 + 100000;
+    const long long cap = timeout_ns / 256 + 100000;
     for (long long it = 0;; ++it) {
         if (*word >= target) return true;
         if (abort && *abort) return false;
         if ((long long)(gtimer() - t0) > timeout_ns || it > cap) return false;
-        __nanosleep(32);
+        __nanosleep(256);
     }
 }
 

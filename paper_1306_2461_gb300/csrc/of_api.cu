@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -40,6 +41,20 @@ int configure_device()
 }  // namespace
 
 namespace of {
+
+static std::atomic<int> g_fail_allocs{0};
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    int n = g_fail_allocs.load();
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 
 // Layout of one plan's workspace (all offsets 256-byte aligned):
 //   pyramid slot 0 | pyramid slot 1 | flow buffer 0 | flow buffer 1 | status word
@@ -241,7 +256,7 @@ int of_create(const of_plan *p, of_handle *out)
     h->plan = *p;
     layout_plan(*p, h->lay);
     cudaGetDevice(&h->device);
-    cudaError_t e = cudaMalloc((void **)&h->ws, h->lay.total);
+    cudaError_t e = dev_malloc((void **)&h->ws, h->lay.total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -371,5 +386,7 @@ const char *of_status_string(int s)
 }
 
 int of_version(void) { return 100; }
+
+int of_debug_fail_allocs(int32_t n) { return of::g_fail_allocs.exchange(n < 0 ? 0 : n); }
 
 }  // extern "C"

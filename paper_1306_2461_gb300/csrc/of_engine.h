@@ -63,6 +63,9 @@ void drop_graphs(of_ctx *h);
 
 // A reusable launch slot for the persistent batch kernel: device and pinned host
 // buffers for the descriptors of up to max_pairs pairs and max_phases phases.
+// cudaMalloc that honours of_debug_fail_allocs (injected out-of-memory failures).
+cudaError_t dev_malloc(void **p, size_t bytes);
+
 struct BatchSlot {
     char *dev = nullptr;
     char *host = nullptr;

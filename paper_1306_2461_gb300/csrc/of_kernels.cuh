@@ -266,9 +266,8 @@ __device__ __forceinline__ void lk_tile_generic(const IterArgs &a, int tile, int
         if (y >= a.H || x >= a.W) continue;
         float s[5];
         box_vsum(S, RH, r, ty, tx, s);
-        float2 f = flow_at<NC>(a, x, y);
         float xu, xv;
-        if (solve2(s, fp64_cond, xu, xv)) f = make_float2(ref.x + xu, ref.y + xv);
+        const float2 f = solve2(s, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv) : flow_at<NC>(a, x, y);
         if (a.fout) {
             a.fout[(size_t)y * a.fout_pitch + x] = f;
         } else {
@@ -583,9 +582,8 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
             const int y = ty0 + 4 * g + j;
             if (y >= a.H) break;
             const float sj[5] = {s[0][j], s[1][j], s[2][j], s[3][j], s[4][j]};
-            float2 f = flow_at<NC>(a, x, y);
             float xu, xv;
-            if (solve2(sj, fp64_cond, xu, xv)) f = make_float2(ref.x + xu, ref.y + xv);
+            const float2 f = solve2(sj, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv) : flow_at<NC>(a, x, y);
             if (a.fout) {
                 a.fout[(size_t)y * a.fout_pitch + x] = f;
             } else {

@@ -306,7 +306,7 @@ int of_server_open_stream(of_server_t s, int32_t H, int32_t W, int32_t *id)
     st.bytes = need;
     int rc = of_create(&p, &st.h);
     for (int b = 0; rc == OF_OK && b < 2; ++b)
-        if (cudaMalloc(&st.raw[b], frame) != cudaSuccess) {
+        if (of::dev_malloc(&st.raw[b], frame) != cudaSuccess) {
             cudaGetLastError();
             rc = OF_ENOMEM;
         }

@@ -74,6 +74,7 @@ def _load():
         "of_get_level": (ctypes.c_int, [vp, i32, i32, vp, vp]),
         "of_window_sums": (ctypes.c_int, [vp, i32, i32, i32, vp, vp]),
         "of_debug_wait_timeout": (ctypes.c_int, [i32]),
+        "of_debug_fail_allocs": (ctypes.c_int, [i32]),
         "of_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "of_version": (ctypes.c_int, []),
     }
