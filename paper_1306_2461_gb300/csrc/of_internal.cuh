@@ -95,7 +95,10 @@ struct PyrArgs {
 // Tile shapes.
 constexpr int LK_TW = 64;    // iteration output tile width
 constexpr int LK_TH = 32;    // iteration output tile height
-constexpr int LK_THREADS = 256;
+#ifndef OF_LK_THREADS
+#define OF_LK_THREADS 256
+#endif
+constexpr int LK_THREADS = OF_LK_THREADS;   // threads per iteration / batch block
 constexpr int PYR_TW = 32;   // pyramid output tile
 constexpr int PYR_TH = 16;
 constexpr int PYR_THREADS = 256;

@@ -121,8 +121,8 @@ __device__ __forceinline__ void sample_grad(const T *I, int pitch, int H, int W,
         const float fx = floorf(px), fy = floorf(py);
         const int x0 = (int)fx, y0 = (int)fy;
         const float ax = px - fx, ay = py - fy;
-        const T *rm = I + (size_t)(y0 - 1) * pitch + x0;
-        const T *r0 = rm + pitch, *r1 = r0 + pitch, *r2 = r1 + pitch;
+        const int o = (y0 - 1) * pitch + x0;
+        const T *rm = I + o, *r0 = I + (o + pitch), *r1 = I + (o + 2 * pitch), *r2 = I + (o + 3 * pitch);
         const float a0 = ldf<NC>(rm), a1 = ldf<NC>(rm + 1);
         const float bm = ldf<NC>(r0 - 1), b0 = ldf<NC>(r0), b1 = ldf<NC>(r0 + 1), b2 = ldf<NC>(r0 + 2);
         const float cm = ldf<NC>(r1 - 1), c0 = ldf<NC>(r1), c1 = ldf<NC>(r1 + 1), c2 = ldf<NC>(r1 + 2);
@@ -138,22 +138,43 @@ __device__ __forceinline__ void sample_grad(const T *I, int pitch, int H, int W,
     }
 }
 
-// Current estimate at (x, y) of the level being iterated.
+// Current estimate at (x, y) of the level being iterated, for a flow mode known at
+// compile time (offsets in 32 bits: a level holds fewer than 2^31 elements).
+template <bool NC, int MODE>
+__device__ __forceinline__ float2 flow_at_m(const IterArgs &a, int x, int y)
+{
+    if constexpr (MODE == FLOW_ZERO) {
+        return make_float2(0.0f, 0.0f);
+    } else if constexpr (MODE == FLOW_SAME) {
+        return ld<NC>(a.fin + (y * a.fin_pitch + x));
+    } else {
+        // 2 * bilinear(coarse; x/2, y/2): weights are 0 or 1/2, indices clamped
+        const int x0 = x >> 1, y0 = y >> 1;
+        const int x1 = min(x0 + 1, a.Wc - 1), y1 = min(y0 + 1, a.Hc - 1);
+        const float ax = (x & 1) ? 0.5f : 0.0f, ay = (y & 1) ? 0.5f : 0.0f;
+        const float2 *r0 = a.fin + y0 * a.fin_pitch, *r1 = a.fin + y1 * a.fin_pitch;
+        const float2 f00 = ld<NC>(r0 + x0), f01 = ld<NC>(r0 + x1);
+        const float2 f10 = ld<NC>(r1 + x0), f11 = ld<NC>(r1 + x1);
+        return make_float2(2.0f * lerpf(lerpf(f00.x, f01.x, ax), lerpf(f10.x, f11.x, ax), ay),
+                           2.0f * lerpf(lerpf(f00.y, f01.y, ax), lerpf(f10.y, f11.y, ax), ay));
+    }
+}
+
+// The same with the mode read at run time.
 template <bool NC>
 __device__ __forceinline__ float2 flow_at(const IterArgs &a, int x, int y)
 {
-    if (a.mode == FLOW_ZERO) return make_float2(0.0f, 0.0f);
-    if (a.mode == FLOW_SAME) return ld<NC>(a.fin + (size_t)y * a.fin_pitch + x);
-    // 2 * bilinear(coarse; x/2, y/2): weights are 0 or 1/2, indices clamped
-    const int x0 = x >> 1, y0 = y >> 1;
-    const int x1 = min(x0 + 1, a.Wc - 1), y1 = min(y0 + 1, a.Hc - 1);
-    const float ax = (x & 1) ? 0.5f : 0.0f, ay = (y & 1) ? 0.5f : 0.0f;
-    const float2 f00 = ld<NC>(a.fin + (size_t)y0 * a.fin_pitch + x0);
-    const float2 f01 = ld<NC>(a.fin + (size_t)y0 * a.fin_pitch + x1);
-    const float2 f10 = ld<NC>(a.fin + (size_t)y1 * a.fin_pitch + x0);
-    const float2 f11 = ld<NC>(a.fin + (size_t)y1 * a.fin_pitch + x1);
-    return make_float2(2.0f * lerpf(lerpf(f00.x, f01.x, ax), lerpf(f10.x, f11.x, ax), ay),
-                       2.0f * lerpf(lerpf(f00.y, f01.y, ax), lerpf(f10.y, f11.y, ax), ay));
+    if (a.mode == FLOW_ZERO) return flow_at_m<NC, FLOW_ZERO>(a, x, y);
+    if (a.mode == FLOW_SAME) return flow_at_m<NC, FLOW_SAME>(a, x, y);
+    return flow_at_m<NC, FLOW_UPSAMPLE>(a, x, y);
+}
+
+// MODE < 0: read the mode at run time.
+template <bool NC, int MODE>
+__device__ __forceinline__ float2 flow_mode(const IterArgs &a, int x, int y)
+{
+    if constexpr (MODE < 0) return flow_at<NC>(a, x, y);
+    else return flow_at_m<NC, MODE>(a, x, y);
 }
 
 // Horizontal pass of the box sums: S[c][ry][tx] = sum_{k=0..2r} P[c][ry][tx+k], left to right.
@@ -203,7 +224,7 @@ __device__ __forceinline__ bool solve2(const float s[5], float fp64_cond, float 
         return true;
     }
     if (!(det > 1e-6f * tr * tr)) return false;
-    const float inv = 1.0f / det;
+    const float inv = __fdividef(1.0f, det);   // det < 2^126 for any sums of 16-bit data
     xu = (c * d - b * e) * inv;
     xv = (a * e - b * d) * inv;
     return true;
@@ -303,7 +324,10 @@ template <int R> struct FixedTile {
     static constexpr int OFF_BAR = (OFF_FBOX + FBOX + 1) / 2 * 2;   // 8-byte aligned mbarrier
     static constexpr int OFF_BOX = OFF_BAR + 2;                      // 4 ints: box bounds
     static constexpr int SMEM_FLOATS = OFF_BOX + 4;
-    static constexpr int MIN_BLOCKS = R <= 6 ? 3 : 2;
+#ifndef OF_LK_MIN_BLOCKS
+#define OF_LK_MIN_BLOCKS 3
+#endif
+    static constexpr int MIN_BLOCKS = R <= 6 ? OF_LK_MIN_BLOCKS : 2;
 };
 
 constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's row copies
@@ -438,7 +462,7 @@ template <int R> __device__ __forceinline__ void lk_tile_init(float *smem)
 
 // Returns false if the staging copy did not complete in time (then OF_ETIMEOUT is in
 // *a.status, nothing of the tile was written, and the block must stop).
-template <typename T, bool NC, int R>
+template <typename T, bool NC, int R, int MODE>
 __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float fp64_cond, float *smem,
                                               uint32_t &phase)
 {
@@ -449,7 +473,7 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
     int *s_box = reinterpret_cast<int *>(smem + F::OFF_BOX);
     const int tyi = tile / a.tiles_x;
     const int ty0 = tyi * LK_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
-    const float2 ref = flow_at<NC>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + LK_TH / 2, a.H - 1));
+    const float2 ref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + LK_TH / 2, a.H - 1));
     const T *I1 = static_cast<const T *>(a.I1);
     const T *I2 = static_cast<const T *>(a.I2);
     if (threadIdx.x == 0) {
@@ -466,7 +490,7 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
         const int ry = i / F::RW, rx = i - ry * F::RW;
         const int y = ty0 - R + ry, x = tx0 - R + rx;
         if ((unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W) {
-            const float2 f = flow_at<NC>(a, x, y);
+            const float2 f = flow_mode<NC, MODE>(a, x, y);
             const int ix = (int)fminf(fmaxf((float)x + f.x, 0.0f), (float)(a.W - 1));
             const int iy = (int)fminf(fmaxf((float)y + f.y, 0.0f), (float)(a.H - 1));
             lx0 = min(lx0, ix - 1);
@@ -535,7 +559,7 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
             const int ry = i / F::RW, rx = i - ry * F::RW;
             const int y = ty0 - R + ry, x = tx0 - R + rx;
             in[u] = i < F::NREG && (unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W;
-            f[u] = in[u] ? flow_at<NC>(a, x, y) : make_float2(0.0f, 0.0f);
+            f[u] = in[u] ? flow_mode<NC, MODE>(a, x, y) : make_float2(0.0f, 0.0f);
         }
 #pragma unroll
         for (int u = 0; u < S1; ++u) {
@@ -551,7 +575,7 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
                 else
                     sample_grad<NC>(I2, a.pitch, a.H, a.W, (float)x + f[u].x, (float)y + f[u].y, Iw, gx, gy);
                 const float e =
-                    ldf<NC>(I1 + (size_t)y * a.pitch + x) - Iw + gx * (f[u].x - ref.x) + gy * (f[u].y - ref.y);
+                    ldf<NC>(I1 + (y * a.pitch + x)) - Iw + gx * (f[u].x - ref.x) + gy * (f[u].y - ref.y);
                 p0 = gx * gx;
                 p1 = gx * gy;
                 p2 = gy * gy;
@@ -583,7 +607,7 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
             if (y >= a.H) break;
             const float sj[5] = {s[0][j], s[1][j], s[2][j], s[3][j], s[4][j]};
             float xu, xv;
-            const float2 f = solve2(sj, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv) : flow_at<NC>(a, x, y);
+            const float2 f = solve2(sj, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv) : flow_mode<NC, MODE>(a, x, y);
             if (a.fout) {
                 a.fout[(size_t)y * a.fout_pitch + x] = f;
             } else {
@@ -605,7 +629,7 @@ __device__ __forceinline__ bool lk_tile(const IterArgs &a, int tile, int r, floa
         lk_tile_generic<T, NC>(a, tile, r, fp64_cond, smem);
         return true;
     } else {
-        return lk_tile_fixed<T, NC, R>(a, tile, fp64_cond, smem, phase);
+        return lk_tile_fixed<T, NC, R, -1>(a, tile, fp64_cond, smem, phase);
     }
 }
 
