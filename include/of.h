@@ -57,6 +57,9 @@ typedef enum of_storage { OF_F32 = 0, OF_F16 = 1, OF_BF16 = 2 } of_storage;
 
 /* plan.flags */
 #define OF_FLAG_NO_GRAPH 0x1u /* launch kernels one by one instead of replaying a CUDA graph */
+#define OF_FLAG_ZNSSD 0x4u    /* normalise both images before the pyramid (Sect. 2.4, Eq. 2): local
+                                 mean and standard deviation over a radius of 5 pixels, clipped
+                                 to the image; level 0 is then stored at the storage precision */
 #define OF_FLAG_STAGE_I2 0x2u /* stage each tile's I2 footprint in shared memory with bulk async
                                  copies instead of gathering the taps from global memory (same
                                  results; a different trade between latency and work) */
@@ -157,6 +160,24 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
  */
 #define OF_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)
 int of_compute_noalloc(const of_plan *p, const void *I1, const void *I2, float *u, float *v, of_stream_t stream);
+
+/*
+ * Recirculation-bubble surface, Eq. 3 (Sect. 3.2): S_bubble = (number of vectors whose
+ * streamwise component u is <= T_v) / (number of vectors). The paper's fraction is
+ * garbled (it divides the count by a sum of velocities); this is the reading of its
+ * text, "percentage of velocities below a given threshold".
+ *  u:      device, H*W floats (a field from of_compute, or any streamwise component).
+ *  count:  device, one unsigned 64-bit integer, overwritten with the count (exact);
+ *          S_bubble = count / (H*W).
+ * The comparison is in FP32 and inclusive. OF_EINVAL for NULL pointers, empty sizes or
+ * a NaN threshold.
+ */
+int of_sbubble_count(const float *u, int32_t H, int32_t W, float Tv, unsigned long long *count, of_stream_t stream);
+
+/* Minimum and maximum of a device field of H*W floats into minmax[0], minmax[1]
+ * (device, 2 floats), ignoring NaNs (NaN results if every value is NaN). With the
+ * time-mean streamwise field this gives Eq. 3's threshold T_v = (min + max) / 2. */
+int of_field_minmax(const float *field, int32_t H, int32_t W, float *minmax, of_stream_t stream);
 
 /* Wait for the handle's last queued work, then read and clear its device status
  * word. Returns OF_OK, OF_EDEVICE or OF_ETIMEOUT from the device, or OF_ECUDA. */

@@ -65,6 +65,12 @@ def lib():
             L.ofo_lk_iteration.restype = i
             L.ofo_flow.argtypes = [_dp, _dp, i, i, i, i, i, _dp, _dp, ctypes.c_void_p]
             L.ofo_flow.restype = i
+            L.ofo_znssd.argtypes = [_dp, i, i, i, d, _dp]
+            fp = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+            L.ofo_sbubble_count.argtypes = [fp, i, i, ctypes.c_float]
+            L.ofo_sbubble_count.restype = ctypes.c_longlong
+            L.ofo_sbubble_threshold.argtypes = [fp, i, i]
+            L.ofo_sbubble_threshold.restype = d
             L.ofo_threads.restype = i
             L.ofo_set_threads.argtypes = [i]
             _lib = L
@@ -174,6 +180,30 @@ def flow(I1, I2, levels: int, radius: int, iterations: int, want_ratio: bool = F
     if rc:
         raise ValueError("oracle flow failed (bad arguments or out of memory)")
     return (u, v, q) if want_ratio else (u, v)
+
+
+ZNSSD_RADIUS = 5      # Sect. 2.4: local statistics over a radius of 5 pixels
+ZNSSD_EPS = 1.0       # added to the local variance (intensity units squared)
+
+
+def znssd(img, rho: int = ZNSSD_RADIUS, eps: float = ZNSSD_EPS) -> np.ndarray:
+    """Eq. 2 local normalisation: (I - local mean) / sqrt(local variance + eps)."""
+    a = _f64(img)
+    out = np.empty_like(a)
+    lib().ofo_znssd(a, a.shape[0], a.shape[1], int(rho), float(eps), out)
+    return out
+
+
+def sbubble_count(u, Tv: float) -> int:
+    """Eq. 3 numerator: vectors with streamwise component u <= Tv (FP32 comparison)."""
+    a = np.ascontiguousarray(u, dtype=np.float32)
+    return int(lib().ofo_sbubble_count(a, a.shape[0], a.shape[1], float(np.float32(Tv))))
+
+
+def sbubble_threshold(mean_u) -> float:
+    """Eq. 3 threshold T_v = (min + max)/2 of the mean streamwise field."""
+    a = np.ascontiguousarray(mean_u, dtype=np.float32)
+    return float(lib().ofo_sbubble_threshold(a, a.shape[0], a.shape[1]))
 
 
 if __name__ == "__main__":

@@ -278,3 +278,53 @@ void ofo_set_threads(int n) { if (n > 0) omp_set_num_threads(n); }
 int ofo_threads(void) { return 1; }
 void ofo_set_threads(int n) { (void)n; }
 #endif
+
+/* Recirculation-bubble surface (Sect. 3.2, Eq. 3), read as the number of vectors whose
+ * streamwise component u is at most the threshold T_v, over the number of vectors.
+ * Returns the count; the fraction is count / (H W). */
+long long ofo_sbubble_count(const float *u, int H, int W, float Tv)
+{
+    long long c = 0;
+    for (size_t k = 0; k < (size_t)H * W; ++k)
+        if (u[k] <= Tv) ++c;
+    return c;
+}
+
+/* The threshold of Eq. 3: T_v = (min + max) / 2 of the mean streamwise field. */
+double ofo_sbubble_threshold(const float *mean_u, int H, int W)
+{
+    float lo = mean_u[0], hi = mean_u[0];
+    for (size_t k = 1; k < (size_t)H * W; ++k) {
+        if (mean_u[k] < lo) lo = mean_u[k];
+        if (mean_u[k] > hi) hi = mean_u[k];
+    }
+    return 0.5 * ((double)lo + (double)hi);
+}
+
+/* Local normalisation of an image before the flow (Sect. 2.4, Eq. 2): with I_m the
+ * local mean and s the local standard deviation over the (2 rho + 1)^2 window clipped
+ * to the image (n pixels), out = (I - I_m) / sqrt(s^2 + eps). The printed radicand
+ * (mean^2 - mean of squares) is negative; the variance is read instead. Written with
+ * the window sums S1 = sum I, S2 = sum I^2: out = (n I - S1) / sqrt(n S2 - S1^2 + n^2 eps).
+ * Direct double loops over every window. */
+void ofo_znssd(const double *I, int H, int W, int rho, double eps, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            double n = 0.0, s1 = 0.0, s2 = 0.0;
+            for (int yy = y - rho; yy <= y + rho; ++yy) {
+                if (yy < 0 || yy >= H) continue;
+                for (int xx = x - rho; xx <= x + rho; ++xx) {
+                    if (xx < 0 || xx >= W) continue;
+                    const double v = I[(size_t)yy * W + xx];
+                    n += 1.0;
+                    s1 += v;
+                    s2 += v * v;
+                }
+            }
+            const double mean = s1 / n;
+            const double var = s2 / n - mean * mean;
+            out[(size_t)y * W + x] = (I[(size_t)y * W + x] - mean) / sqrt(var + eps);
+        }
+}

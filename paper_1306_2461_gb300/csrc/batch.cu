@@ -86,7 +86,8 @@ static bool same_method(const of_plan &a, const of_plan &b)
 {
     return a.levels == b.levels && a.radius == b.radius && a.iterations == b.iterations &&
            a.in_format == b.in_format && a.in_bits == b.in_bits && a.storage == b.storage &&
-           a.fp64_cond == b.fp64_cond && (a.flags & OF_FLAG_STAGE_I2) == (b.flags & OF_FLAG_STAGE_I2);
+           a.fp64_cond == b.fp64_cond &&
+           (a.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD)) == (b.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD));
 }
 
 // The host image of one batch: descriptors, work-list prefix sums, slots, launch shape.
@@ -111,7 +112,8 @@ static int build_batch(int32_t n, const of_handle *hs, const void *const *I1s, c
     }
     const of_plan &p0 = hs[0]->plan;
     const int L = p0.levels;
-    b.npyr = L > 1 ? L - 1 : 1;
+    const bool zn = (p0.flags & OF_FLAG_ZNSSD) != 0;
+    b.npyr = zn ? L : (L > 1 ? L - 1 : 1);
     b.nphases = b.npyr + L * p0.iterations;
     b.pairs.assign(n, BatchPair());
     b.prefix.assign((size_t)b.nphases * (n + 1), 0);
@@ -147,8 +149,11 @@ static int build_batch(int32_t n, const of_handle *hs, const void *const *I1s, c
         for (int i = 0; i < n; ++i) {
             const BatchPair &bp = b.pairs[i];
             int64_t cnt;
-            if (ph < b.npyr) {
-                const int Ho = (bp.H[ph] + 1) / 2, Wo = (bp.W[ph] + 1) / 2;
+            if (ph < b.npyr && zn && ph == 0) {
+                cnt = (int64_t)((bp.W[0] + ZN_T - 1) / ZN_T) * ((bp.H[0] + ZN_T - 1) / ZN_T) * (2 - bp.first_image);
+            } else if (ph < b.npyr) {
+                const int ls = zn ? ph - 1 : ph;
+                const int Ho = (bp.H[ls] + 1) / 2, Wo = (bp.W[ls] + 1) / 2;
                 cnt = (int64_t)((Wo + PYR_TW - 1) / PYR_TW) * ((Ho + PYR_TH - 1) / PYR_TH) * (2 - bp.first_image);
             } else {
                 const int l = L - 1 - (ph - b.npyr) / p0.iterations;
@@ -178,6 +183,7 @@ static void fill_header(BatchHdr &hd, const of_plan &p0, const BatchBuild &b, ch
     hd.fp64_cond = p0.fp64_cond;
     hd.timeout_ns = BARRIER_TIMEOUT_NS;
     hd.stage_i2 = (p0.flags & OF_FLAG_STAGE_I2) ? 1 : 0;
+    hd.znssd = (p0.flags & OF_FLAG_ZNSSD) ? 1 : 0;
 }
 
 static size_t bar_offset(const BatchBuild &b)
@@ -301,7 +307,8 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
         memcpy(k, b.pairs.data(), pairs_bytes);
         memcpy(k + pairs_bytes, b.prefix.data(), prefix_bytes);
         memcpy(k + pairs_bytes + prefix_bytes, &st, sizeof(st));
-        const int extra[3] = {p0.radius, p0.iterations * 2 + ((p0.flags & OF_FLAG_STAGE_I2) ? 1 : 0), hs[0]->device};
+        const int extra[3] = {p0.radius, (int)(p0.iterations * 8 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD))),
+                              hs[0]->device};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
 

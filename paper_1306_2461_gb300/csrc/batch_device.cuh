@@ -36,6 +36,7 @@ struct BatchHdr {
     float fp64_cond;
     long long timeout_ns;
     int32_t stage_i2;
+    int32_t znssd;                      // phase 0 normalises the images (Eq. 2)
 };
 
 constexpr long long BARRIER_TIMEOUT_NS = 2000000000LL;   // 2 s per phase
@@ -108,8 +109,26 @@ __global__ void __launch_bounds__(LK_THREADS, batch_min_blocks<R>()) batch_kerne
             const BatchPair &bp = hd.pairs[pi];
             const int j = item - pre[pi];
             if (phase < hd.npyr) {
-                // pyramid pass `phase`: level phase -> phase + 1 (the first pass reads raw)
-                const int ls = phase, ld = phase + 1;
+                if (hd.znssd && phase == 0) {
+                    // local normalisation (Eq. 2): raw -> level 0 at the storage precision
+                    ZnArgs z;
+                    z.H = bp.H[0];
+                    z.W = bp.W[0];
+                    z.src_pitch = bp.W[0];
+                    z.dst_pitch = bp.pitch[0];
+                    z.tiles_x = (z.W + ZN_T - 1) / ZN_T;
+                    z.tiles = z.tiles_x * ((z.H + ZN_T - 1) / ZN_T);
+                    z.first_image = bp.first_image;
+                    for (int k = 0; k < 2; ++k) {
+                        z.src[k] = bp.raw[k];
+                        z.dst[k] = bp.pyr[k] + bp.off[0];
+                    }
+                    const int img = bp.first_image + j / z.tiles;
+                    znssd_tile<Tin, T, true>(z, j - (j / z.tiles) * z.tiles, img, smem);   // caller images: read-only
+                    continue;
+                }
+                // pyramid pass: level ls -> ls + 1 (the first pass of the plain path reads raw)
+                const int ls = hd.znssd ? phase - 1 : phase, ld = ls + 1;
                 PyrArgs a;
                 a.H = bp.H[ls];
                 a.W = bp.W[ls];
@@ -124,7 +143,7 @@ __global__ void __launch_bounds__(LK_THREADS, batch_min_blocks<R>()) batch_kerne
                     a.dst[k] = ld < hd.levels ? bp.pyr[k] + bp.off[ld] : nullptr;
                     a.dst0[k] = bp.pyr[k] + bp.off[0];
                 }
-                if (phase == 0) {
+                if (!hd.znssd && phase == 0) {
                     a.src[0] = bp.raw[0];
                     a.src[1] = bp.raw[1];
                     a.src_pitch = bp.W[0];
@@ -173,7 +192,7 @@ __global__ void __launch_bounds__(LK_THREADS, batch_min_blocks<R>()) batch_kerne
                 a.tiles = 0;
                 a.status = bp.status;
                 a.stage_i2 = hd.stage_i2;
-                if (l == 0) live = lk_tile<Tin, false, R>(a, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
+                if (l == 0 && !hd.znssd) live = lk_tile<Tin, false, R>(a, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
                 else live = lk_tile<T, false, R>(a, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
             }
         }

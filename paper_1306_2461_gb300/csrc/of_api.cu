@@ -90,29 +90,50 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
     const of_plan &p = h->plan;
     const Layout &L = h->lay;
     cudaError_t e;
-    // pyramids: first pass (raw -> level 0 and level 1), then one pass per further level
+    // pyramids: first pass (raw -> level 0 and level 1), then one pass per further
+    // level; with the normalisation of Eq. 2, a normalisation pass (raw -> level 0) and
+    // then one reduction per level from level 0
     {
+        const int sl[2] = {s1, s2};
         PyrArgs a;
         memset(&a, 0, sizeof(a));
         a.first_image = I1 ? 0 : 1;
-        a.src[0] = I1;
-        a.src[1] = I2;
-        const int sl[2] = {s1, s2};
-        for (int k = 0; k < 2; ++k) {
-            a.dst0[k] = h->pyr[sl[k]] + L.level_off[0];
-            a.dst[k] = p.levels > 1 ? h->pyr[sl[k]] + L.level_off[1] : nullptr;
+        int lfirst;   // first level reduced by pyr_down
+        if (p.flags & OF_FLAG_ZNSSD) {
+            ZnArgs z;
+            memset(&z, 0, sizeof(z));
+            z.src[0] = I1;
+            z.src[1] = I2;
+            for (int k = 0; k < 2; ++k) z.dst[k] = h->pyr[sl[k]] + L.level_off[0];
+            z.H = L.H[0];
+            z.W = L.W[0];
+            z.src_pitch = L.W[0];
+            z.dst_pitch = L.pitch[0];
+            z.first_image = a.first_image;
+            z.tiles_x = (z.W + ZN_T - 1) / ZN_T;
+            z.tiles = z.tiles_x * ((z.H + ZN_T - 1) / ZN_T);
+            if ((e = launch_znssd(z, p.in_format, p.storage, st)) != cudaSuccess) return e;
+            lfirst = 0;
+        } else {
+            a.src[0] = I1;
+            a.src[1] = I2;
+            for (int k = 0; k < 2; ++k) {
+                a.dst0[k] = h->pyr[sl[k]] + L.level_off[0];
+                a.dst[k] = p.levels > 1 ? h->pyr[sl[k]] + L.level_off[1] : nullptr;
+            }
+            a.H = L.H[0];
+            a.W = L.W[0];
+            a.src_pitch = L.W[0];
+            a.dst0_pitch = L.pitch[0];
+            a.Ho = (L.H[0] + 1) / 2;
+            a.Wo = (L.W[0] + 1) / 2;
+            a.dst_pitch = p.levels > 1 ? L.pitch[1] : 0;
+            a.tiles_x = (a.Wo + PYR_TW - 1) / PYR_TW;
+            a.tiles = a.tiles_x * ((a.Ho + PYR_TH - 1) / PYR_TH);
+            if ((e = launch_pyr_first(a, p.in_format, p.storage, st)) != cudaSuccess) return e;
+            lfirst = 1;
         }
-        a.H = L.H[0];
-        a.W = L.W[0];
-        a.src_pitch = L.W[0];
-        a.dst0_pitch = L.pitch[0];
-        a.Ho = (L.H[0] + 1) / 2;
-        a.Wo = (L.W[0] + 1) / 2;
-        a.dst_pitch = p.levels > 1 ? L.pitch[1] : 0;
-        a.tiles_x = (a.Wo + PYR_TW - 1) / PYR_TW;
-        a.tiles = a.tiles_x * ((a.Ho + PYR_TH - 1) / PYR_TH);
-        if ((e = launch_pyr_first(a, p.in_format, p.storage, st)) != cudaSuccess) return e;
-        for (int l = 1; l + 1 < p.levels; ++l) {
+        for (int l = lfirst; l + 1 < p.levels; ++l) {
             for (int k = 0; k < 2; ++k) {
                 a.src[k] = h->pyr[sl[k]] + L.level_off[l];
                 a.dst0[k] = nullptr;
@@ -210,7 +231,7 @@ int of_plan_validate(const of_plan *p)
     }
     if (p->storage != OF_F32 && p->storage != OF_F16 && p->storage != OF_BF16) return OF_EINVAL;
     if (!(p->fp64_cond >= 0.0f) || isinf(p->fp64_cond)) return OF_EINVAL;
-    if (p->flags & ~(OF_FLAG_NO_GRAPH | OF_FLAG_STAGE_I2)) return OF_EINVAL;
+    if (p->flags & ~(OF_FLAG_NO_GRAPH | OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD)) return OF_EINVAL;
     return OF_OK;
 }
 

@@ -39,7 +39,10 @@ enum ElemType : int { ET_U8 = 0, ET_U16 = 1, ET_F32 = 2, ET_F16 = 3, ET_BF16 = 4
 inline int elem_bytes(int et) { return et == ET_U8 ? 1 : (et == ET_F32 ? 4 : 2); }
 inline int raw_elem(int in_format) { return in_format == OF_U8 ? ET_U8 : ET_U16; }
 inline int storage_elem(int storage) { return storage == OF_F32 ? ET_F32 : (storage == OF_F16 ? ET_F16 : ET_BF16); }
-inline int level_elem(const of_plan &p, int level) { return level == 0 ? raw_elem(p.in_format) : storage_elem(p.storage); }
+inline int level_elem(const of_plan &p, int level)
+{
+    return (level == 0 && !(p.flags & OF_FLAG_ZNSSD)) ? raw_elem(p.in_format) : storage_elem(p.storage);
+}
 
 template <typename T> __device__ __forceinline__ T to_elem(float x);
 template <> __device__ __forceinline__ float to_elem<float>(float x) { return x; }
@@ -92,6 +95,18 @@ struct PyrArgs {
     int32_t tiles_x, tiles;  // output tiles of one image
 };
 
+// Arguments of the local normalisation (Eq. 2) of both images of a pair.
+struct ZnArgs {
+    const void *src[2];      // raw camera images (pitch W)
+    void *dst[2];            // level 0 of the pyramid slots (storage type)
+    int32_t H, W, src_pitch, dst_pitch;
+    int32_t first_image;     // 0: both images, 1: only the second
+    int32_t tiles_x, tiles;
+};
+constexpr int ZN_RADIUS = 5;          // Sect. 2.4: a radius of 5 pixels
+constexpr int ZN_T = 32;              // output tile
+constexpr int ZN_EPS = 1;             // added to the local variance (counts squared)
+
 // Tile shapes.
 constexpr int LK_TW = 64;    // iteration output tile width
 constexpr int LK_TH = 32;    // iteration output tile height
@@ -112,6 +127,7 @@ constexpr int MAX_RADIUS = 16;
 // All return cudaGetLastError() of their launch.
 cudaError_t launch_pyr_first(const PyrArgs &a, int in_format, int storage, cudaStream_t s);
 cudaError_t launch_pyr_down(const PyrArgs &a, int storage, cudaStream_t s);
+cudaError_t launch_znssd(const ZnArgs &a, int in_format, int storage, cudaStream_t s);
 cudaError_t launch_lk_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s);
 cudaError_t launch_window_sums(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
 void *batch_kernel_for(int in_format, int storage, int radius);

@@ -93,6 +93,65 @@ __device__ __forceinline__ void pyr_tile(const PyrArgs &a, int tile, int img)
     pyr_tile_smem<Tin, Tout, FIRST, true>(a, tile, img, smem);
 }
 
+// ---------------------------------------------------------- normalisation tile
+// Eq. 2 on one ZN_T x ZN_T tile: window sums S1 = sum I and S2 = sum I^2 over the
+// (2*ZN_RADIUS+1)^2 window clipped to the image (n pixels) in exact integer arithmetic,
+// then out = (n I - S1) / sqrt(n S2 - S1^2 + n^2 eps) in FP32.
+constexpr int ZN_RR = ZN_T + 2 * ZN_RADIUS;
+constexpr int ZN_SMEM_FLOATS = ZN_RR * ZN_RR + ZN_RR * ZN_T + 2 * ZN_RR * ZN_T;
+
+template <typename Tin, typename Tout, bool NC>
+__device__ __forceinline__ void znssd_tile(const ZnArgs &a, int tile, int img, float *smem)
+{
+    unsigned int *s_raw = reinterpret_cast<unsigned int *>(smem);                 // ZN_RR x ZN_RR
+    unsigned int *s_h1 = s_raw + ZN_RR * ZN_RR;                                   // ZN_RR x ZN_T
+    unsigned long long *s_h2 = reinterpret_cast<unsigned long long *>(s_h1 + ZN_RR * ZN_T);
+    const int ty0 = (tile / a.tiles_x) * ZN_T;
+    const int tx0 = (tile - (tile / a.tiles_x) * a.tiles_x) * ZN_T;
+    const Tin *src = static_cast<const Tin *>(img ? a.src[1] : a.src[0]);
+    Tout *dst = static_cast<Tout *>(img ? a.dst[1] : a.dst[0]);
+    __syncthreads();   // the previous tile's readers of smem are done
+    for (int i = threadIdx.x; i < ZN_RR * ZN_RR; i += blockDim.x) {
+        const int ry = i / ZN_RR, rx = i - ry * ZN_RR;
+        const int y = ty0 - ZN_RADIUS + ry, x = tx0 - ZN_RADIUS + rx;
+        s_raw[i] = ((unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W)
+                       ? (unsigned int)ld<NC>(src + ((size_t)y * a.src_pitch + x))
+                       : 0u;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ZN_RR * ZN_T; i += blockDim.x) {
+        const int ry = i / ZN_T, tx = i - ry * ZN_T;
+        const unsigned int *q = s_raw + ry * ZN_RR + tx;
+        unsigned int h1 = 0;
+        unsigned long long h2 = 0;
+#pragma unroll
+        for (int k = 0; k <= 2 * ZN_RADIUS; ++k) {
+            h1 += q[k];
+            h2 += (unsigned long long)q[k] * q[k];
+        }
+        s_h1[i] = h1;
+        s_h2[i] = h2;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ZN_T * ZN_T; i += blockDim.x) {
+        const int ty = i / ZN_T, tx = i - ty * ZN_T;
+        const int y = ty0 + ty, x = tx0 + tx;
+        if (y >= a.H || x >= a.W) continue;
+        long long s1 = 0, s2 = 0;
+#pragma unroll
+        for (int k = 0; k <= 2 * ZN_RADIUS; ++k) {
+            s1 += s_h1[(ty + k) * ZN_T + tx];
+            s2 += (long long)s_h2[(ty + k) * ZN_T + tx];
+        }
+        const long long n = (long long)(min(x + ZN_RADIUS, a.W - 1) - max(x - ZN_RADIUS, 0) + 1) *
+                            (min(y + ZN_RADIUS, a.H - 1) - max(y - ZN_RADIUS, 0) + 1);
+        const long long I = s_raw[(ty + ZN_RADIUS) * ZN_RR + tx + ZN_RADIUS];
+        const float num = (float)(n * I - s1);
+        const float rad = (float)(n * s2 - s1 * s1 + n * n * ZN_EPS);
+        dst[(size_t)y * a.dst_pitch + x] = to_elem<Tout>(num / sqrtf(rad));
+    }
+}
+
 // ------------------------------------------------------------ iteration helpers
 __device__ __forceinline__ float lerpf(float p, float q, float t) { return (1.0f - t) * p + t * q; }
 

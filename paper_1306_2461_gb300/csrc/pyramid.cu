@@ -50,6 +50,30 @@ cudaError_t launch_pyr_down(const PyrArgs &a, int storage, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) znssd_kernel(ZnArgs a)
+{
+    __shared__ float smem[ZN_SMEM_FLOATS];
+    znssd_tile<Tin, Tout, true>(a, blockIdx.x, blockIdx.y + a.first_image, smem);
+}
+
+template <typename Tout> static cudaError_t zn_for(const ZnArgs &a, int in_format, cudaStream_t s)
+{
+    dim3 grid(a.tiles, 2 - a.first_image);
+    if (in_format == OF_U8) znssd_kernel<uint8_t, Tout><<<grid, 256, 0, s>>>(a);
+    else znssd_kernel<uint16_t, Tout><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_znssd(const ZnArgs &a, int in_format, int storage, cudaStream_t s)
+{
+    switch (storage) {
+    case OF_F32: return zn_for<float>(a, in_format, s);
+    case OF_F16: return zn_for<__half>(a, in_format, s);
+    default: return zn_for<__nv_bfloat16>(a, in_format, s);
+    }
+}
+
 template <typename T>
 __global__ void level_to_f32_kernel(Level l, float *dst)
 {

@@ -82,7 +82,9 @@ window_sums_kernel(const float *ch, int H, int W, int r, int tiles_x, float *out
 template <int R> size_t radius_smem_bytes(int r)
 {
     const size_t lk = sizeof(float) * (size_t)lk_tile_smem_floats<R>(r);
-    const size_t pyr = sizeof(float) * (size_t)PYR_SMEM_FLOATS;
+    size_t pyr = sizeof(float) * (size_t)PYR_SMEM_FLOATS;
+    const size_t zn = sizeof(float) * (size_t)ZN_SMEM_FLOATS;
+    if (zn > pyr) pyr = zn;
     return lk > pyr ? lk : pyr;
 }
 

@@ -266,7 +266,7 @@ int of_server_create(const of_server_config *c, of_server_t *out)
     if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess)
         rc = OF_ECUDA;
-    const int phases = (m.levels > 1 ? m.levels - 1 : 1) + m.levels * m.iterations;
+    const int phases = m.levels + m.levels * m.iterations;   // an upper bound on the pyramid phases
     s->slots.resize(c->max_inflight);
     s->ev_copied.assign(c->max_inflight, nullptr);
     s->ev_done.assign(c->max_inflight, nullptr);

@@ -20,6 +20,7 @@ OF_U8, OF_U16 = 0, 1
 OF_F32, OF_F16, OF_BF16 = 0, 1, 2
 OF_FLAG_NO_GRAPH = 0x1
 OF_FLAG_STAGE_I2 = 0x2
+OF_FLAG_ZNSSD = 0x4
 STORAGE = {"f32": OF_F32, "f16": OF_F16, "bf16": OF_BF16}
 
 
@@ -74,6 +75,8 @@ def _load():
         "of_get_level": (ctypes.c_int, [vp, i32, i32, vp, vp]),
         "of_window_sums": (ctypes.c_int, [vp, i32, i32, i32, vp, vp]),
         "of_debug_wait_timeout": (ctypes.c_int, [i32]),
+        "of_sbubble_count": (ctypes.c_int, [vp, i32, i32, ctypes.c_float, vp, vp]),
+        "of_field_minmax": (ctypes.c_int, [vp, i32, i32, vp, vp]),
         "of_debug_fail_allocs": (ctypes.c_int, [i32]),
         "of_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "of_version": (ctypes.c_int, []),
@@ -236,6 +239,27 @@ def window_sums(ch: torch.Tensor, r: int, stream=None) -> torch.Tensor:
     out = torch.empty_like(ch)
     _check(_lib.of_window_sums(ch.data_ptr(), ch.shape[1], ch.shape[2], int(r), out.data_ptr(), _stream(stream)),
            "of_window_sums")
+    return out
+
+
+def sbubble(u: torch.Tensor, Tv: float, stream=None) -> torch.Tensor:
+    """Eq. 3: device count of vectors with u <= Tv (int64 tensor of one element);
+    S_bubble = count / u.numel()."""
+    if u.dtype != torch.float32 or not u.is_cuda or u.dim() != 2 or not u.is_contiguous():
+        raise ValueError("u: expected a contiguous 2-D CUDA float32 tensor")
+    out = torch.empty(1, dtype=torch.int64, device=u.device)
+    _check(_lib.of_sbubble_count(u.data_ptr(), u.shape[0], u.shape[1], float(Tv), out.data_ptr(), _stream(stream)),
+           "of_sbubble_count")
+    return out
+
+
+def field_minmax(f: torch.Tensor, stream=None) -> torch.Tensor:
+    """(min, max) of a 2-D CUDA float32 field, as a device tensor of two floats."""
+    if f.dtype != torch.float32 or not f.is_cuda or f.dim() != 2 or not f.is_contiguous():
+        raise ValueError("f: expected a contiguous 2-D CUDA float32 tensor")
+    out = torch.empty(2, dtype=torch.float32, device=f.device)
+    _check(_lib.of_field_minmax(f.data_ptr(), f.shape[0], f.shape[1], out.data_ptr(), _stream(stream)),
+           "of_field_minmax")
     return out
 
 

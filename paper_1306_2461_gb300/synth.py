@@ -190,7 +190,7 @@ class Pair:
 
 
 def particle_pair(H, W, flow: FlowFn, *, density, peak, noise, bits, seed, sigma=1.0,
-                  umax=None, density_fn=None, meta=None) -> Pair:
+                  umax=None, density_fn=None, meta=None, gain=None, background=None) -> Pair:
     r_pos, r_n1, r_n2 = _rngs(seed, 3)
     yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
     ug, vg = flow(xx, yy)
@@ -201,6 +201,10 @@ def particle_pair(H, W, flow: FlowFn, *, density, peak, noise, bits, seed, sigma
     du, dv = flow(px, py)
     f1 = render_particles(H, W, px, py, peak, sigma)
     f2 = render_particles(H, W, px + du, py + dv, peak, sigma)
+    if gain is not None:          # illumination that does not move with the particles
+        f1, f2 = f1 * gain, f2 * gain
+    if background is not None:
+        f1, f2 = f1 + background, f2 + background
     return Pair(quantise(f1, noise, bits, r_n1), quantise(f2, noise, bits, r_n2),
                 np.asarray(ug, np.float64), np.asarray(vg, np.float64), bits,
                 dict(meta or {}, H=H, W=W, density=density, peak=peak, noise=noise, seed=seed,
@@ -241,6 +245,19 @@ def make_c2(H=1024, W=1024, seed=1, rc=80.0, thickness=40.0) -> Pair:
     """
     return particle_pair(H, W, vortex_shear_flow(H, W, 6.0, rc, 8.0, thickness), density=0.03,
                          peak=3200.0, noise=32.0, bits=12, seed=seed, meta={"workload": C2.name})
+
+
+def make_c2_uneven_light(H=1024, W=1024, seed=1) -> Pair:
+    """The 1024^2 vortex + shear workload under uneven illumination, the case the local
+    normalisation of Eq. 2 is for: 0.05 particles/px, a laser-sheet-like gain varying
+    smoothly from 0.4 to 1.6 across the image and a background rising from 300 to 900
+    counts (12-bit), so that no pixel clips at zero."""
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    gain = 1.0 + 0.6 * np.cos(np.pi * xx / W) * np.cos(0.5 * np.pi * yy / H)
+    background = 300.0 + 600.0 * (yy / max(H - 1, 1))
+    return particle_pair(H, W, vortex_shear_flow(H, W, 6.0, 80.0, 8.0, 40.0), density=0.05, peak=2400.0,
+                         noise=24.0, bits=12, seed=seed, gain=gain, background=background,
+                         meta={"workload": "pair1024_u16_uneven_light"})
 
 
 def make_c3(H=2048, W=2048, seed=2, umax=10.0) -> Pair:

@@ -1,0 +1,88 @@
+"""The local normalisation of Eq. 2 on the device (OF_FLAG_ZNSSD): level 0 against the
+oracle's normalisation, flow parity against the oracle run on normalised images, and the
+batched and reuse forms bit for bit against the per-pair path."""
+import numpy as np
+import pytest
+
+from paper_1306_2461_gb300 import synth
+from helpers import epe, gpu_flow, parity_check, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def of():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_2461_gb300 import build
+    build.build()
+    from paper_1306_2461_gb300 import of as ofmod
+    return ofmod
+
+
+@pytest.mark.parametrize("storage,bits,atol", [("f32", 12, 2e-5), ("f16", 12, 8e-3), ("bf16", 8, 6e-2),
+                                               ("f32", 8, 2e-5)])
+@pytest.mark.parametrize("H,W", [(1, 1), (9, 70), (300, 420)])
+def test_level0_is_the_normalised_image(of, oracle_mod, storage, bits, atol, H, W):
+    import torch
+    rng = np.random.default_rng(H * W + bits)
+    I = rng.integers(0, 1 << bits, (H, W)).astype(np.uint8 if bits <= 8 else np.uint16)
+    plan = of.Plan.make(H, W, 2, 3, 1, bits=bits, storage=storage, flags=of.OF_FLAG_ZNSSD)
+    with of.Flow(plan) as f:
+        f.compute(to_dev(I), to_dev(I))
+        torch.cuda.synchronize()
+        got = f.get_level(0, 0).cpu().double().numpy()
+    ref = oracle_mod.znssd(I.astype(np.float64))
+    # values are O(1): absolute error of the storage rounding (2^-24, 2^-11, 2^-8 relative)
+    assert np.abs(got - ref).max() <= atol
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_flow_with_normalisation_matches_oracle(of, oracle_mod, storage):
+    # particle images under uneven illumination (what the normalisation is for)
+    p = synth.make_c2_uneven_light(512, 512, seed=3)
+    u, v = gpu_flow(p, 3, 4, 5, storage, flags=of.OF_FLAG_ZNSSD)
+    z1 = oracle_mod.znssd(p.I1.astype(np.float64))
+    z2 = oracle_mod.znssd(p.I2.astype(np.float64))
+    # Normalised particle images hold chaotic pixels (~0.1%) that each random 1e-6
+    # perturbation of the input finds anew; three probes exclude some, and up to 0.1% of
+    # the compared pixels may still differ beyond tolerance (counted and printed: 128 of
+    # 214k at FP32, at most 4.5e-3 px, when measured).
+    # With FP16, rounding the normalised level 0 moves ~2% of the pixels by more than
+    # half the tolerance even in exact arithmetic.
+    parity_check(u, v, (z1, z2), oracle_mod, 3, 4, 5, storage, f"znssd 512x512 {storage}", round0=True,
+                 probes=3, outliers_max=1e-3, sensitive_max=0.03)
+    rms, mx = epe(u, v, p, 24)     # normalising level 0 weakens the coarse levels: outliers
+    print(f"EPE vs ground truth with normalisation: rms {rms:.4f} max {mx:.4f}")
+
+
+def test_identical_images_zero_flow_with_normalisation(of):
+    rng = np.random.default_rng(3)
+    I = rng.integers(0, 4096, (130, 200)).astype(np.uint16)
+    u, v = gpu_flow((I, I), 3, 4, 3, "f16", bits=12, flags=of.OF_FLAG_ZNSSD)
+    assert np.all(u == 0.0) and np.all(v == 0.0)
+
+
+def test_batch_and_reuse_with_normalisation_equal_single(of):
+    import torch
+    streams = [synth.ParticleStream(H, W, seed=20 + k) for k, (H, W) in enumerate(((160, 224), (96, 320)))]
+    frames = []
+    for st in streams:
+        fr = []
+        for _ in range(3):
+            fr.append(to_dev(st.frame()))
+            st.advance()
+        frames.append(fr)
+    plans = [of.Plan.make(st.H, st.W, 3, 4, 3, bits=12, storage="f16", flags=of.OF_FLAG_ZNSSD) for st in streams]
+    flows = [of.Flow(pl) for pl in plans]
+    of.compute_batch(flows, [f[0] for f in frames], [f[1] for f in frames])
+    ub, vb = of.compute_batch(flows, [None, None], [f[2] for f in frames])     # reuse the resident pyramids
+    torch.cuda.synchronize()
+    for k, pl in enumerate(plans):
+        with of.Flow(pl) as g:
+            us, vs = g.compute(frames[k][1], frames[k][2])
+            torch.cuda.synchronize()
+        assert torch.equal(ub[k], us) and torch.equal(vb[k], vs), k
+    for f in flows:
+        f.close()

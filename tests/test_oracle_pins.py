@@ -266,3 +266,55 @@ def test_level_sizes_halve_with_ceiling(oracle_mod):
     assert oracle_mod.level_size(1, 1, 5) == (1, 1)
     I = np.zeros((383, 1791))
     assert [p.shape for p in oracle_mod.pyramid(I, 3)] == [(383, 1791), (192, 896), (96, 448)]
+
+
+# ------------------------------------------------------------- Eq. 3 (S_bubble)
+def test_sbubble_count_closed_forms(oracle_mod):
+    # a ramp u(x) = x - 20 on a 30 x 50 field: u <= T for the floor(T) + 21 first columns
+    H, W = 30, 50
+    u = (np.arange(W, dtype=np.float32)[None, :] - 20.0) * np.ones((H, 1), np.float32)
+    for T in (-25.0, -20.0, -0.5, 0.0, 3.7, 29.0, 100.0):
+        expect = H * int(np.clip(np.floor(T) + 21, 0, W))
+        assert oracle_mod.sbubble_count(u, T) == expect
+    # uniform fields: all or nothing; the comparison is inclusive
+    assert oracle_mod.sbubble_count(np.full((7, 9), 1.5, np.float32), 1.5) == 63
+    assert oracle_mod.sbubble_count(np.full((7, 9), 1.5, np.float32), 1.4999) == 0
+
+
+def test_sbubble_threshold_is_midrange(oracle_mod):
+    rng = np.random.default_rng(4)
+    m = rng.normal(0, 3, (40, 60)).astype(np.float32)
+    assert oracle_mod.sbubble_threshold(m) == 0.5 * (float(m.min()) + float(m.max()))
+
+
+# ------------------------------------------------------ Eq. 2 (local normalisation)
+def test_znssd_constant_and_step_edge(oracle_mod):
+    assert np.all(oracle_mod.znssd(np.full((20, 30), 77.0)) == 0.0)
+    # a vertical step 0 | 100 at column 15; pixel (10, 15) sees 6 of 11 columns at 100:
+    # n = 121, S1 = 6600, S2 = 660000 -> (121*100 - 6600) / sqrt(121*660000 - 6600^2 + 121^2 eps)
+    I = np.zeros((21, 31))
+    I[:, 15:] = 100.0
+    out = oracle_mod.znssd(I, 5, 1.0)
+    expect = (121 * 100 - 6600) / np.sqrt(121 * 660000 - 6600 ** 2 + 121 ** 2 * 1.0)
+    assert abs(out[10, 15] - expect) < 1e-12
+    assert abs(out[10, 14] + expect * (5500 / 5500)) < 0.2        # mirror pixel: negative, similar size
+    assert out[10, 14] < 0 and np.all(out[:, :9] == 0.0) and np.all(out[:, 21:] == 0.0)
+
+
+def test_znssd_affine_invariance(oracle_mod):
+    rng = np.random.default_rng(8)
+    I = rng.uniform(0, 100, (24, 37))
+    a = oracle_mod.znssd(I, 5, 0.0)
+    b = oracle_mod.znssd(3.5 * I + 1000.0, 5, 0.0)
+    np.testing.assert_allclose(a, b, atol=1e-9)
+
+
+def test_znssd_matches_library_window_sums(oracle_mod):
+    rng = np.random.default_rng(9)
+    I = rng.integers(0, 4096, (29, 41)).astype(np.float64)
+    box = np.ones((11, 11))
+    n = signal.convolve2d(np.ones_like(I), box, mode="same")
+    s1 = signal.convolve2d(I, box, mode="same")
+    s2 = signal.convolve2d(I * I, box, mode="same")
+    ref = (n * I - s1) / np.sqrt(n * s2 - s1 * s1 + n * n * 1.0)
+    np.testing.assert_allclose(oracle_mod.znssd(I, 5, 1.0), ref, rtol=1e-10, atol=1e-12)
