@@ -230,6 +230,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the single-pair and e2e legs")
+    ap.add_argument("--table1", action="store_true",
+                    help="sweep levels {3,4} x iterations 1..7 at 1792x384, r = 10 (synthetic Table 1) and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -253,6 +255,10 @@ def main():
     from paper_1306_2461_gb300 import build as libbuild
     libbuild.build()
     from paper_1306_2461_gb300 import of, synth
+    if args.table1:
+        if rank == 0:
+            print(json.dumps(table1_sweep(torch, of, synth)), flush=True)
+        return 0
 
     B = args.batch
     src = [synth.make_c2(H, W, seed=1 + 7919 * (i + rank * DISTINCT)) for i in range(DISTINCT)]
@@ -415,6 +421,63 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
                   "path": "pinned host frames -> of_compute_batch -> pinned host u, v (one stream)"}
     out["serving"] = serving_leg(torch, synth)
     return out
+
+
+def table1_sweep(torch, of, synth, batch=16, reps=20):
+    """Synthetic analogue of Table 1: for levels in {3, 4} and iterations 1..7 at the
+    paper's region of interest (1792 x 384, 8-bit, r = 10), the error of the field
+    relative to the 7-iteration field of the same level count (RMS of the difference over
+    RMS of that field, in %), and fields/s of the plain FP32 single pair and of the
+    FP16 batched launch (batch pairs per launch)."""
+    Hr, Wr, r = 384, 1792, 10
+    p = synth.make_bfs(Hr, Wr, seed=5)
+    I1 = torch.from_numpy(p.I1).cuda()
+    I2 = torch.from_numpy(p.I2).cuda()
+    s = torch.cuda.Stream()
+    rows = []
+    m = (r + 2) * 4
+    for L in (3, 4):
+        fields = {}
+        for n in range(1, 8):
+            plan = of.Plan.make(Hr, Wr, L, r, n, bits=8, storage="f32")
+            with of.Flow(plan) as f, torch.cuda.stream(s):
+                for _ in range(3):
+                    u, v = f.compute(I1, I2, stream=s)
+                s.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                for _ in range(reps):
+                    f.compute(I1, I2, u, v, stream=s)
+                b.record(s)
+                s.synchronize()
+                single = reps / (a.elapsed_time(b) / 1000.0)
+                fields[n] = (u.cpu().double().numpy(), v.cpu().double().numpy())
+            plan16 = of.Plan.make(Hr, Wr, L, r, n, bits=8, storage="f16")
+            flows = [of.Flow(plan16) for _ in range(batch)]
+            with torch.cuda.stream(s):
+                for _ in range(3):
+                    of.compute_batch(flows, [I1] * batch, [I2] * batch, stream=s)
+                s.synchronize()
+                a.record(s)
+                for _ in range(max(3, reps // 4)):
+                    of.compute_batch(flows, [I1] * batch, [I2] * batch, stream=s)
+                b.record(s)
+                s.synchronize()
+            batched = batch * max(3, reps // 4) / (a.elapsed_time(b) / 1000.0)
+            for f in flows:
+                f.close()
+            rows.append({"levels": L, "iterations": n, "single_f32_fields_per_s": single,
+                         "batched_f16_fields_per_s": batched})
+        u7, v7 = fields[7]
+        ref = np.sqrt(np.mean((u7 ** 2 + v7 ** 2)[m:-m, m:-m]))
+        for row in rows[-7:]:
+            un, vn = fields[row["iterations"]]
+            d = np.sqrt(np.mean(((un - u7) ** 2 + (vn - v7) ** 2)[m:-m, m:-m]))
+            row["error_pct_vs_7_iterations"] = 100.0 * d / ref
+            e = np.sqrt((un - p.u_gt) ** 2 + (vn - p.v_gt) ** 2)[m:-m, m:-m]
+            row["epe_rms_px"] = float(np.sqrt((e ** 2).mean()))
+    return {"table1_synthetic": rows, "config": {"workload": "roi1792x384_u8_bfs", "radius": r,
+                                                 "batch": batch}}
 
 
 def serving_leg(torch, synth, rate_per_stream=125.0, warmup_s=0.25, measure_s=2.0, frames_per_stream=3):

@@ -260,6 +260,31 @@ def make_c2_uneven_light(H=1024, W=1024, seed=1) -> Pair:
                          meta={"workload": "pair1024_u16_uneven_light"})
 
 
+def bfs_flow(H: int, W: int, U=8.0, back=-1.0, y_layer=0.6, delta=20.0, n_vort=5, peak=2.0, rc=20.0) -> FlowFn:
+    """A flow shaped like the region downstream of a backward-facing step (Sect. 2.3): a
+    shear layer at y = y_layer*H between the free stream (U px/frame, upper part of the
+    image) and a slow recirculation (back px/frame, lower part), with a row of vortices
+    rolled up along the layer. Max |u| ~ U + peak."""
+    yl = y_layer * H
+
+    def f(x, y):
+        ux = back + 0.5 * (U - back) * (1.0 - np.tanh((y - yl) / delta))
+        uy = np.zeros(np.shape(y), np.float64)
+        for k in range(n_vort):
+            a, b = lamb_oseen(x, y, (k + 0.5) * W / n_vort, yl, peak, rc, sign=1.0)
+            ux = ux + a
+            uy = uy + b
+        return ux, uy
+    return f
+
+
+def make_bfs(H=384, W=1792, seed=5) -> Pair:
+    """The region of interest of the paper's setup (1792 x 384, 8-bit camera, Sect. 2.4)
+    with particles as the 256^2 workload, displaced by bfs_flow()."""
+    return particle_pair(H, W, bfs_flow(H, W), density=0.02, peak=200.0, noise=2.0, bits=8, seed=seed,
+                         meta={"workload": "roi1792x384_u8_bfs"})
+
+
 def make_c3(H=2048, W=2048, seed=2, umax=10.0) -> Pair:
     """12-bit, 0.03 particles/px except 0.002 in rows [0.4H, 0.6H); band-limited flow
     with wavenumbers |k| <= min(H,W)/64 (cutoff 1/64 px^-1), max |u| = 10 px."""

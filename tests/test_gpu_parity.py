@@ -272,3 +272,12 @@ def test_injected_allocation_failures_are_clean(of):
         torch.cuda.synchronize()
         assert bool((u == 0).all())
     assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+
+
+def test_paper_roi_radius10(of, oracle_mod):
+    # the paper's region of interest and window (1792 x 384, r = 10) with 4 levels
+    p = synth.make_bfs()
+    u, v = gpu_flow(p, 4, 10, 2, "f32")
+    check(u, v, p, oracle_mod, 4, 10, 2, "f32", "1792x384 u8 r10")
+    rms, mx = epe(u, v, p, (10 + 2) * 8)
+    print(f"EPE vs ground truth: rms {rms:.4f} max {mx:.4f}")
