@@ -65,6 +65,10 @@ def lib():
             L.ofo_lk_iteration.restype = i
             L.ofo_flow.argtypes = [_dp, _dp, i, i, i, i, i, _dp, _dp, ctypes.c_void_p]
             L.ofo_flow.restype = i
+            L.ofo_flow_variant.argtypes = [_dp, _dp, i, i, i, i, i, _dp, _dp, ctypes.c_void_p, i]
+            L.ofo_flow_variant.restype = i
+            L.ofo_lk_iteration_i1grad.argtypes = [_dp, _dp, i, i, i, _dp, _dp, _dp, _dp, _dp]
+            L.ofo_lk_iteration_i1grad.restype = i
             L.ofo_znssd.argtypes = [_dp, i, i, i, d, _dp]
             fp = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
             L.ofo_sbubble_count.argtypes = [fp, i, i, ctypes.c_float]
@@ -166,8 +170,20 @@ def lk_iteration(P1, P2, u, v, r: int):
     return un, vn, q
 
 
-def flow(I1, I2, levels: int, radius: int, iterations: int, want_ratio: bool = False):
-    """Dense coarse-to-fine flow at level 0. Returns (u, v) or (u, v, min det/tr^2 at level 0)."""
+def lk_iteration_i1grad(P1, P2, u, v, r: int):
+    """One iteration of the variant linearised with the first image's gradient (window
+    matrix fixed per level). Returns (u', v', det/tr^2)."""
+    a, b = _f64(P1), _f64(P2)
+    H, W = a.shape
+    un, vn, q = (np.empty((H, W)) for _ in range(3))
+    if lib().ofo_lk_iteration_i1grad(a, b, H, W, int(r), _f64(u), _f64(v), un, vn, q):
+        raise MemoryError("oracle iteration failed")
+    return un, vn, q
+
+
+def flow(I1, I2, levels: int, radius: int, iterations: int, want_ratio: bool = False, i1grad: bool = False):
+    """Dense coarse-to-fine flow at level 0. Returns (u, v) or (u, v, min det/tr^2 at level 0).
+    i1grad=True: the variant with the first image's gradient (window matrix fixed per level)."""
     a, b = _f64(I1), _f64(I2)
     if a.shape != b.shape or a.ndim != 2:
         raise ValueError("I1 and I2 must be 2-D arrays of one shape")
@@ -175,8 +191,8 @@ def flow(I1, I2, levels: int, radius: int, iterations: int, want_ratio: bool = F
     u = np.empty((H, W))
     v = np.empty((H, W))
     q = np.empty((H, W)) if want_ratio else None
-    rc = lib().ofo_flow(a, b, H, W, int(levels), int(radius), int(iterations), u, v,
-                        q.ctypes.data if q is not None else None)
+    rc = lib().ofo_flow_variant(a, b, H, W, int(levels), int(radius), int(iterations), u, v,
+                                q.ctypes.data if q is not None else None, 1 if i1grad else 0)
     if rc:
         raise ValueError("oracle flow failed (bad arguments or out of memory)")
     return (u, v, q) if want_ratio else (u, v)

@@ -195,6 +195,45 @@ int ofo_lk_iteration(const double *P1, const double *P2, int H, int W, int r,
     return 0;
 }
 
+/* Variant with the window matrix fixed per level (the FOLKI lineage): the image is
+ * linearised with the gradient of the FIRST image at integer pixels (central
+ * difference, indices clamped, /2) instead of the gradient of I2 at the displaced
+ * position, so that [Sa Sb; Sb Sc] depends on I1 only. Per iteration, with
+ * e~ = I1 - I2w + g1x u_k + g1y v_k, solve [Sa Sb; Sb Sc] u_{k+1} = [sum g1x e~; sum g1y e~]
+ * (same guard as ofo_lk_iteration). */
+int ofo_lk_iteration_i1grad(const double *P1, const double *P2, int H, int W, int r,
+                            const double *u, const double *v, double *u_new, double *v_new,
+                            double *ratio)
+{
+    const size_t N = (size_t)H * W;
+    double *buf = (double *)malloc(sizeof(double) * N * 13);
+    if (!buf) return -1;
+    double *Iw = buf, *g1x = buf + N, *g1y = buf + 2 * N;
+    double *p[5], *S[5];
+    for (int k = 0; k < 5; ++k) { p[k] = buf + (3 + k) * N; S[k] = buf + (8 + k) * N; }
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t k = (size_t)y * W + x;
+            const int xm = clampi(x - 1, 0, W - 1), xp = clampi(x + 1, 0, W - 1);
+            const int ym = clampi(y - 1, 0, H - 1), yp = clampi(y + 1, 0, H - 1);
+            g1x[k] = (P1[(size_t)y * W + xp] - P1[(size_t)y * W + xm]) / 2.0;
+            g1y[k] = (P1[(size_t)yp * W + x] - P1[(size_t)ym * W + x]) / 2.0;
+            Iw[k] = ofo_bilinear(P2, H, W, x + u[k], y + v[k]);
+        }
+    for (size_t k = 0; k < N; ++k) {
+        const double et = P1[k] - Iw[k] + g1x[k] * u[k] + g1y[k] * v[k];
+        p[0][k] = g1x[k] * g1x[k];
+        p[1][k] = g1x[k] * g1y[k];
+        p[2][k] = g1y[k] * g1y[k];
+        p[3][k] = g1x[k] * et;
+        p[4][k] = g1y[k] * et;
+    }
+    for (int k = 0; k < 5; ++k) ofo_window_sum(p[k], H, W, r, S[k]);
+    ofo_solve(S[0], S[1], S[2], S[3], S[4], u, v, (int)N, u_new, v_new, ratio, NULL);
+    free(buf);
+    return 0;
+}
+
 /* Level sizes of the pyramid: level 0 is H x W, level l+1 is ceil of half of level l. */
 void ofo_level_size(int H, int W, int level, int *Hl, int *Wl)
 {
@@ -206,8 +245,8 @@ void ofo_level_size(int H, int W, int level, int *Hl, int *Wl)
  * displacement on the coarsest level, run `iters` iterations per level, propagate.
  * u, v: H x W outputs (level 0). ratio_min (optional, H x W): the smallest det/tr^2
  * each pixel saw over the level-0 iterations, for locating near-singular pixels. */
-int ofo_flow(const double *I1, const double *I2, int H, int W, int levels, int r, int iters,
-             double *u, double *v, double *ratio_min)
+int ofo_flow_variant(const double *I1, const double *I2, int H, int W, int levels, int r, int iters,
+                     double *u, double *v, double *ratio_min, int i1grad)
 {
     if (H <= 0 || W <= 0 || levels < 1 || r < 0 || iters < 0) return -1;
     double **P1 = (double **)calloc((size_t)levels, sizeof(double *));
@@ -250,7 +289,9 @@ int ofo_flow(const double *I1, const double *I2, int H, int W, int levels, int r
             memcpy(fv, gv, sizeof(double) * n);
         }
         for (int it = 0; it < iters; ++it) {
-            if (ofo_lk_iteration(P1[l], P2[l], h, w, r, fu, fv, gu, gv, rt)) { rc = -1; goto done; }
+            const int it_rc = i1grad ? ofo_lk_iteration_i1grad(P1[l], P2[l], h, w, r, fu, fv, gu, gv, rt)
+                                     : ofo_lk_iteration(P1[l], P2[l], h, w, r, fu, fv, gu, gv, rt);
+            if (it_rc) { rc = -1; goto done; }
             memcpy(fu, gu, sizeof(double) * n);
             memcpy(fv, gv, sizeof(double) * n);
             if (l == 0 && ratio_min)
@@ -267,6 +308,12 @@ done:
     free(P1); free(P2); free(Hs); free(Ws);
     free(fu); free(fv); free(gu); free(gv); free(rt);
     return rc;
+}
+
+int ofo_flow(const double *I1, const double *I2, int H, int W, int levels, int r, int iters,
+             double *u, double *v, double *ratio_min)
+{
+    return ofo_flow_variant(I1, I2, H, W, levels, r, iters, u, v, ratio_min, 0);
 }
 
 /* Number of OpenMP threads the oracle will use (1 when built without OpenMP). */

@@ -18,7 +18,8 @@ MUTANTS = {
     "gradient_sign": ("ofo_bilinear(I2, H, W, px + 1.0, py) - ofo_bilinear(I2, H, W, px - 1.0, py)",
                       "ofo_bilinear(I2, H, W, px - 1.0, py) - ofo_bilinear(I2, H, W, px + 1.0, py)"),
     "dropped_linearisation_term": (" + gx[k] * u[k]", ""),
-    "residual_sign": ("P1[k] - Iw[k]", "Iw[k] - P1[k]"),
+    "residual_sign": ("double e = P1[k] - Iw[k]", "double e = Iw[k] - P1[k]"),
+    "i1grad_residual_sign": ("double et = P1[k] - Iw[k]", "double et = Iw[k] - P1[k]"),
     "transposed_solve": ("*xu = (c * d0 - b * e0) / det;", "*xu = (a * d0 - b * e0) / det;"),
     "wrong_product": ("p[1][k] = gx[k] * gy[k];", "p[1][k] = gx[k] * gx[k];"),
     "window_off_by_one": ("for (int dx = -r; dx <= r; ++dx)", "for (int dx = -r; dx < r; ++dx)"),
@@ -28,6 +29,11 @@ MUTANTS = {
     "bilinear_weights_swapped": ("(1.0 - ax) * img[(size_t)y0 * W + x0] + ax * img[(size_t)y0 * W + x1]",
                                  "ax * img[(size_t)y0 * W + x0] + (1.0 - ax) * img[(size_t)y0 * W + x1]"),
     "bilinear_row_not_interpolated": ("const int y1 = y0 + 1 < H ? y0 + 1 : H - 1;", "const int y1 = y0;"),
+    "i1grad_dropped_linearisation_term": (" + g1x[k] * u[k]", ""),
+    "i1grad_gradient_sign": ("g1x[k] = (P1[(size_t)y * W + xp] - P1[(size_t)y * W + xm]) / 2.0;",
+                             "g1x[k] = (P1[(size_t)y * W + xm] - P1[(size_t)y * W + xp]) / 2.0;"),
+    "i1grad_gradient_rows_swapped": ("g1y[k] = (P1[(size_t)yp * W + x] - P1[(size_t)ym * W + x]) / 2.0;",
+                                     "g1y[k] = (P1[(size_t)y * W + xp] - P1[(size_t)y * W + xm]) / 2.0;"),
     "guard_inverted": ("if (det <= OFO_SINGULAR_EPS * tr * tr) return 0;",
                        "if (det > OFO_SINGULAR_EPS * tr * tr) return 0;"),
 }

@@ -318,3 +318,48 @@ def test_znssd_matches_library_window_sums(oracle_mod):
     s2 = signal.convolve2d(I * I, box, mode="same")
     ref = (n * I - s1) / np.sqrt(n * s2 - s1 * s1 + n * n * 1.0)
     np.testing.assert_allclose(oracle_mod.znssd(I, 5, 1.0), ref, rtol=1e-10, atol=1e-12)
+
+
+# ------------------------------- variant with the first image's gradient (FOLKI)
+def test_i1grad_variant_pins(oracle_mod):
+    # identical images: exactly zero; integer translation: exact fixed point reached;
+    # sub-pixel translation: recovered to < 0.01 px on average
+    rng = np.random.default_rng(3)
+    I = rng.integers(0, 4096, (64, 80)).astype(np.float64)
+    u, v = oracle_mod.flow(I, I, 3, 4, 3, i1grad=True)
+    assert np.all(u == 0.0) and np.all(v == 0.0)
+    d = (3.0, -2.0)
+    I1, I2 = synth.translated_texture_pair(128, 160, d, seed=1)
+    u, v = oracle_mod.flow(I1, I2, 3, 4, 15, i1grad=True)
+    m = 24
+    assert np.abs(valid(u, m) - d[0]).max() < 1e-6 and np.abs(valid(v, m) - d[1]).max() < 1e-6
+    d = (1.3, -0.7)
+    I1, I2 = synth.translated_texture_pair(128, 128, d, seed=1)
+    u, v = oracle_mod.flow(I1, I2, 2, 10, 12, i1grad=True)
+    m = 24
+    assert abs(valid(u, m).mean() - d[0]) < 0.01 and abs(valid(v, m).mean() - d[1]) < 0.01
+
+
+def test_i1grad_iteration_matches_library_solve(oracle_mod):
+    # integer flow field: exact lookups; the window matrix from the first image only
+    H, W, r = 26, 31, 3
+    rng = np.random.default_rng(12)
+    P1 = rng.uniform(0, 200, (H, W))
+    P2 = rng.uniform(0, 200, (H, W))
+    u = rng.integers(-2, 3, (H, W)).astype(np.float64)
+    v = rng.integers(-2, 3, (H, W)).astype(np.float64)
+    y, x = np.mgrid[0:H, 0:W]
+    Iw = P2[np.clip(y + v.astype(int), 0, H - 1), np.clip(x + u.astype(int), 0, W - 1)]
+    gx = (P1[y, np.clip(x + 1, 0, W - 1)] - P1[y, np.clip(x - 1, 0, W - 1)]) / 2
+    gy = (P1[np.clip(y + 1, 0, H - 1), x] - P1[np.clip(y - 1, 0, H - 1), x]) / 2
+    et = P1 - Iw + gx * u + gy * v
+    box = np.ones((2 * r + 1, 2 * r + 1))
+    S = [signal.convolve2d(c, box, mode="same") for c in (gx * gx, gx * gy, gy * gy, gx * et, gy * et)]
+    M = np.stack([np.stack([S[0], S[1]], -1), np.stack([S[1], S[2]], -1)], -2)
+    ref = np.linalg.solve(M, np.stack([S[3], S[4]], -1)[..., None])[..., 0]
+    u1, v1, q = oracle_mod.lk_iteration_i1grad(P1, P2, u, v, r)
+    np.testing.assert_allclose(u1, ref[..., 0], rtol=1e-7, atol=1e-7)
+    np.testing.assert_allclose(v1, ref[..., 1], rtol=1e-7, atol=1e-7)
+    # and it differs from the I2-gradient iteration (a swapped gradient would be caught)
+    u2, v2, _ = oracle_mod.lk_iteration(P1, P2, u, v, r)
+    assert np.abs(u2 - u1).max() > 1e-3
