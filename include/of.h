@@ -63,6 +63,13 @@ typedef enum of_storage { OF_F32 = 0, OF_F16 = 1, OF_BF16 = 2 } of_storage;
 #define OF_FLAG_STAGE_I2 0x2u /* stage each tile's I2 footprint in shared memory with bulk async
                                  copies instead of gathering the taps from global memory (same
                                  results; a different trade between latency and work) */
+#define OF_FLAG_I1GRAD 0x8u   /* the FOLKI-lineage variant (Sect. 2.4): linearise with the gradient
+                                 of the FIRST image at integer pixels (central difference, clamped)
+                                 instead of the second image's gradient at the displaced position.
+                                 The window matrix then depends on I1 only and is summed once per
+                                 level; each iteration sums two channels. Per-pair calls only:
+                                 of_compute_batch and of_server_create return OF_EINVAL for it.
+                                 The workspace grows by one float4 per level-0 pixel. */
 
 /*
  * Problem statement (Sect. 2.4): image size of the region of interest, number of

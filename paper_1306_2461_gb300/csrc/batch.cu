@@ -104,7 +104,7 @@ static int build_batch(int32_t n, const of_handle *hs, const void *const *I1s, c
     if (n < 0 || n > 65536 || !hs || !I1s || !I2s || !us || !vs) return OF_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!hs[i] || !I2s[i] || !us[i] || !vs[i]) return OF_EINVAL;
-        if (!same_method(hs[i]->plan, hs[0]->plan)) return OF_EINVAL;
+        if (!same_method(hs[i]->plan, hs[0]->plan) || (hs[i]->plan.flags & OF_FLAG_I1GRAD)) return OF_EINVAL;
         if (!I1s[i] && !hs[i]->has_prev) return OF_ESTATE;
         if (hs[i]->device != hs[0]->device) return OF_EINVAL;
         for (int j = 0; j < i; ++j)

@@ -161,6 +161,8 @@ __global__ void __launch_bounds__(LK_THREADS, batch_min_blocks<R>()) batch_kerne
                 const int it = k - (k / hd.iterations) * hd.iterations;
                 const int cur = k & 1;
                 IterArgs a;
+                a.hess = nullptr;
+                a.hess_pitch = 0;
                 a.I1 = bp.pyr[0] + bp.off[l];
                 a.I2 = bp.pyr[1] + bp.off[l];
                 a.H = bp.H[l];

@@ -25,6 +25,26 @@ cudaError_t launch_window_sums(const float *ch, int H, int W, int r, float *out,
     }
 }
 
+#define OF_CASE_I1H(R) \
+    case R: return i1h_launch<R>(a, elem, radius, s);
+cudaError_t launch_i1_hess(const HessArgs &a, int elem, int radius, cudaStream_t s)
+{
+    switch (radius) {
+        OF_RADII(OF_CASE_I1H)
+    default: return i1h_launch<0>(a, elem, radius, s);
+    }
+}
+
+#define OF_CASE_I1(R) \
+    case R: return i1_launch<R>(a, elem, radius, fp64_cond, s);
+cudaError_t launch_i1_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s)
+{
+    switch (radius) {
+        OF_RADII(OF_CASE_I1)
+    default: return i1_launch<0>(a, elem, radius, fp64_cond, s);
+    }
+}
+
 #define OF_CASE_BK(R) \
     case R: return batch_kernel_ptr<R>(in_format, storage);
 void *batch_kernel_for(int in_format, int storage, int radius)

@@ -66,12 +66,7 @@ extern "C" int of_compute_noalloc(const of_plan *p, const void *I1, const void *
     h.plan = *p;
     h.lay = lay;
     cudaGetDevice(&h.device);
-    h.ws = ws;
-    h.pyr[0] = ws;
-    h.pyr[1] = ws + lay.pyr_bytes;
-    h.flow[0] = reinterpret_cast<float2 *>(ws + 2 * lay.pyr_bytes);
-    h.flow[1] = reinterpret_cast<float2 *>(ws + 2 * lay.pyr_bytes + lay.flow_bytes);
-    h.status = reinterpret_cast<int *>(ws + 2 * lay.pyr_bytes + 2 * lay.flow_bytes);
+    of::assign_workspace(&h, ws);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(h.status, 0, sizeof(int), st) != cudaSuccess) return OF_ECUDA;
     return of::enqueue_pair(&h, I1, I2, u, v, 0, 1, st) == cudaSuccess ? OF_OK : OF_ECUDA;

@@ -58,6 +58,7 @@ cudaError_t dev_malloc(void **p, size_t bytes)
 
 // Layout of one plan's workspace (all offsets 256-byte aligned):
 //   pyramid slot 0 | pyramid slot 1 | flow buffer 0 | flow buffer 1 | status word
+//   [| window matrices (OF_FLAG_I1GRAD: one float4 per pixel of level 0, reused per level)]
 // A pyramid slot holds levels 0..L-1 of one image: level 0 in the input's integer
 // format, levels >= 1 at the storage precision. A flow buffer holds the interleaved
 // (u, v) float2 field of the largest level.
@@ -78,7 +79,21 @@ void layout_plan(const of_plan &p, Layout &L)
     }
     L.pyr_bytes = off;
     L.flow_bytes = align_up((size_t)L.pitch[0] * L.H[0] * sizeof(float2), kAlign);
-    L.total = 2 * L.pyr_bytes + 2 * L.flow_bytes + kAlign;
+    L.hess_off = 2 * L.pyr_bytes + 2 * L.flow_bytes + kAlign;
+    L.hess_bytes = (p.flags & OF_FLAG_I1GRAD) ? align_up((size_t)L.pitch[0] * L.H[0] * sizeof(float4), kAlign) : 0;
+    L.total = L.hess_off + L.hess_bytes;
+}
+
+void assign_workspace(of_ctx *h, char *ws)
+{
+    const Layout &L = h->lay;
+    h->ws = ws;
+    h->pyr[0] = ws;
+    h->pyr[1] = ws + L.pyr_bytes;
+    h->flow[0] = reinterpret_cast<float2 *>(ws + 2 * L.pyr_bytes);
+    h->flow[1] = reinterpret_cast<float2 *>(ws + 2 * L.pyr_bytes + L.flow_bytes);
+    h->status = reinterpret_cast<int *>(ws + 2 * L.pyr_bytes + 2 * L.flow_bytes);
+    h->hess = L.hess_bytes ? reinterpret_cast<float4 *>(ws + L.hess_off) : nullptr;
 }
 
 // Queue the whole method for one pair (Sect. 2.4): pyramids, then n iterations on every
@@ -151,8 +166,22 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
         }
     }
     // iterations
+    const bool i1grad = (p.flags & OF_FLAG_I1GRAD) != 0;
     int cur = 0;
     for (int l = p.levels - 1; l >= 0; --l) {
+        if (i1grad) {
+            // the variant's window matrix of this level, from I1 alone
+            HessArgs ha;
+            ha.I1 = h->pyr[s1] + L.level_off[l];
+            ha.H = L.H[l];
+            ha.W = L.W[l];
+            ha.pitch = L.pitch[l];
+            ha.hess = h->hess;
+            ha.hess_pitch = L.pitch[l];
+            ha.tiles_x = (ha.W + LK_TW - 1) / LK_TW;
+            ha.tiles = ha.tiles_x * ((ha.H + LK_TH - 1) / LK_TH);
+            if ((e = launch_i1_hess(ha, level_elem(p, l), p.radius, st)) != cudaSuccess) return e;
+        }
         for (int it = 0; it < p.iterations; ++it) {
             IterArgs a;
             memset(&a, 0, sizeof(a));
@@ -186,7 +215,14 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
             a.tiles = a.tiles_x * ((a.H + LK_TH - 1) / LK_TH);
             a.status = h->status;
             a.stage_i2 = (p.flags & OF_FLAG_STAGE_I2) ? 1 : 0;
-            if ((e = launch_lk_iter(a, level_elem(p, l), p.radius, p.fp64_cond, st)) != cudaSuccess) return e;
+            if (i1grad) {
+                a.hess = h->hess;
+                a.hess_pitch = L.pitch[l];
+                e = launch_i1_iter(a, level_elem(p, l), p.radius, p.fp64_cond, st);
+            } else {
+                e = launch_lk_iter(a, level_elem(p, l), p.radius, p.fp64_cond, st);
+            }
+            if (e != cudaSuccess) return e;
             cur = 1 - cur;
         }
     }
@@ -231,7 +267,7 @@ int of_plan_validate(const of_plan *p)
     }
     if (p->storage != OF_F32 && p->storage != OF_F16 && p->storage != OF_BF16) return OF_EINVAL;
     if (!(p->fp64_cond >= 0.0f) || isinf(p->fp64_cond)) return OF_EINVAL;
-    if (p->flags & ~(OF_FLAG_NO_GRAPH | OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD)) return OF_EINVAL;
+    if (p->flags & ~(OF_FLAG_NO_GRAPH | OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD)) return OF_EINVAL;
     return OF_OK;
 }
 
@@ -283,11 +319,7 @@ int of_create(const of_plan *p, of_handle *out)
         delete h;
         return map_cuda(e);
     }
-    h->pyr[0] = h->ws;
-    h->pyr[1] = h->ws + h->lay.pyr_bytes;
-    h->flow[0] = reinterpret_cast<float2 *>(h->ws + 2 * h->lay.pyr_bytes);
-    h->flow[1] = reinterpret_cast<float2 *>(h->ws + 2 * h->lay.pyr_bytes + h->lay.flow_bytes);
-    h->status = reinterpret_cast<int *>(h->ws + 2 * h->lay.pyr_bytes + 2 * h->lay.flow_bytes);
+    assign_workspace(h, h->ws);
     if ((e = cudaMemset(h->status, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->ctl, cudaStreamNonBlocking)) != cudaSuccess ||

@@ -18,6 +18,7 @@ struct Layout {
     size_t level_off[MAX_LEVELS];   // byte offset of each level inside a pyramid slot
     size_t pyr_bytes;               // one pyramid slot
     size_t flow_bytes;              // one float2 flow buffer (level 0, pitched)
+    size_t hess_off, hess_bytes;    // window matrices of the first-image-gradient variant (0 bytes otherwise)
     size_t total;
 };
 
@@ -42,6 +43,7 @@ struct of_ctx {
     char *pyr[2] = {nullptr, nullptr};
     float2 *flow[2] = {nullptr, nullptr};
     int *status = nullptr;           // device status word
+    float4 *hess = nullptr;          // OF_FLAG_I1GRAD: (Sa, Sb, Sc, 0) of the level being iterated
     cudaEvent_t done = nullptr;      // recorded after each compute
     cudaStream_t ctl = nullptr;      // private stream for status reads
     bool has_prev = false;           // a previous second image's pyramid is resident
@@ -55,6 +57,8 @@ struct of_ctx {
 
 namespace of {
 
+// Point the handle's buffers into a workspace of lay.total bytes laid out by layout_plan.
+void assign_workspace(of_ctx *h, char *ws);
 cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, float *v, int s1, int s2,
                          cudaStream_t st);
 // Queue one pair through a cached CUDA graph when the stream allows it, else directly.

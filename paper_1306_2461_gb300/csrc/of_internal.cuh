@@ -80,6 +80,17 @@ struct IterArgs {
     int32_t tiles;           // tiles in this level
     int *status;             // the handle's device status word (errors only)
     int32_t stage_i2;        // stage the tile's I2 footprint in shared memory (fixed-radius tile)
+    const float4 *hess;      // first-image-gradient variant: window matrix (Sa, Sb, Sc, 0) of this level
+    int32_t hess_pitch;      // float4 elements per row of hess
+};
+
+// Arguments of the per-level window-matrix pass of the first-image-gradient variant.
+struct HessArgs {
+    const void *I1;          // level image of the first frame
+    int32_t H, W, pitch;
+    float4 *hess;            // output: (Sa, Sb, Sc, 0) per pixel
+    int32_t hess_pitch;
+    int32_t tiles_x, tiles;
 };
 
 // Arguments of one pyramid reduction (both images of a pair at once).
@@ -130,6 +141,10 @@ cudaError_t launch_pyr_down(const PyrArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_znssd(const ZnArgs &a, int in_format, int storage, cudaStream_t s);
 cudaError_t launch_lk_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s);
 cudaError_t launch_window_sums(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
+// The variant linearised with the first image's gradient: window matrix of one level,
+// then iterations that read it from a.hess.
+cudaError_t launch_i1_hess(const HessArgs &a, int elem, int radius, cudaStream_t s);
+cudaError_t launch_i1_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s);
 void *batch_kernel_for(int in_format, int storage, int radius);
 size_t batch_smem_bytes(int radius);
 cudaError_t launch_level_to_f32(const Level &l, int elem, float *dst, cudaStream_t s);
@@ -139,6 +154,8 @@ cudaError_t configure_lk_kernels();   // all kernels with dynamic shared memory,
 // Per-radius instantiations (radius_<R>.cu; R = 0 is the generic kernel).
 template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
+template <int R> cudaError_t i1h_launch(const HessArgs &a, int elem, int r, cudaStream_t s);
+template <int R> cudaError_t i1_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> void *batch_kernel_ptr(int in_format, int storage);
 template <int R> cudaError_t radius_configure();
 template <int R> size_t radius_smem_bytes(int r);

@@ -236,14 +236,15 @@ __device__ __forceinline__ float2 flow_mode(const IterArgs &a, int x, int y)
     else return flow_at_m<NC, MODE>(a, x, y);
 }
 
-// Horizontal pass of the box sums: S[c][ry][tx] = sum_{k=0..2r} P[c][ry][tx+k], left to right.
+// Horizontal pass of the box sums of C planes: S[c][ry][tx] = sum_{k=0..2r} P[c][ry][tx+k], left to right.
+template <int C = 5>
 __device__ __forceinline__ void box_hsum(const float *P, float *S, int RH, int RW, int r)
 {
     const int n = RH * LK_TW;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int ry = i / LK_TW, tx = i - ry * LK_TW;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < C; ++c) {
             const float *q = P + (size_t)c * RH * RW + ry * RW + tx;
             float s = 0.0f;
             for (int k = 0; k <= 2 * r; ++k) s += q[k];
@@ -253,11 +254,12 @@ __device__ __forceinline__ void box_hsum(const float *P, float *S, int RH, int R
 }
 
 // Vertical pass at output (ty, tx): sums of S over rows ty..ty+2r, top to bottom.
-__device__ __forceinline__ void box_vsum(const float *S, int RH, int r, int ty, int tx, float s[5])
+template <int C = 5>
+__device__ __forceinline__ void box_vsum(const float *S, int RH, int r, int ty, int tx, float s[C])
 {
     const int n = RH * LK_TW;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
+    for (int c = 0; c < C; ++c) {
         const float *q = S + c * n + ty * LK_TW + tx;
         float acc = 0.0f;
         for (int k = 0; k <= 2 * r; ++k) acc += q[k * LK_TW];
@@ -448,9 +450,9 @@ __device__ __forceinline__ void box4(const float *v, float o[4])
     o[3] = ((m + v[2 * R + 1]) + v[2 * R + 2]) + v[2 * R + 3];
 }
 
-// Horizontal pass, in place: row ry of plane c becomes, at columns 0..LK_TW-1, the
-// window sums of the outputs of that row.
-template <int R>
+// Horizontal pass, in place: row ry of plane c (c < C) becomes, at columns
+// 0..LK_TW-1, the window sums of the outputs of that row.
+template <int R, int C = 5>
 __device__ __forceinline__ void box_h_inplace(float *P)
 {
     using F = FixedTile<R>;
@@ -458,7 +460,7 @@ __device__ __forceinline__ void box_h_inplace(float *P)
     constexpr int NITEMS = F::RH * NG;
     constexpr int IT = (NITEMS + LK_THREADS - 1) / LK_THREADS;
 #pragma unroll 1
-    for (int c = 0; c < 5; ++c) {
+    for (int c = 0; c < C; ++c) {
         float *Pc = P + c * F::PLANE;
         float4 res[IT];
 #pragma unroll
@@ -494,13 +496,13 @@ __device__ __forceinline__ void box_h_inplace(float *P)
     __syncthreads();
 }
 
-// Vertical pass for the 4 outputs (rows 4g..4g+3, column tx) of every channel.
-template <int R>
-__device__ __forceinline__ void box_v4(const float *P, int g, int tx, float s[5][4])
+// Vertical pass for the 4 outputs (rows 4g..4g+3, column tx) of each of C channels.
+template <int R, int C = 5>
+__device__ __forceinline__ void box_v4(const float *P, int g, int tx, float s[C][4])
 {
     using F = FixedTile<R>;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
+    for (int c = 0; c < C; ++c) {
         const float *col = P + c * F::PLANE + 4 * g * F::RWP + tx;
         float v[2 * R + 4];
 #pragma unroll

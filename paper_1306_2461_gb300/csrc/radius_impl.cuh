@@ -3,6 +3,7 @@
 #pragma once
 
 #include "batch_device.cuh"
+#include "i1grad_kernels.cuh"
 #include "of_internal.cuh"
 #include "of_kernels.cuh"
 
@@ -113,6 +114,40 @@ template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, flo
     return cudaGetLastError();
 }
 
+template <typename T, int R> static cudaError_t i1h_for(const HessArgs &a, int r, cudaStream_t s)
+{
+    i1_hess_kernel<T, R><<<a.tiles, LK_THREADS, sizeof(float) * i1_smem_floats<R>(r, 3), s>>>(a, r);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t i1h_launch(const HessArgs &a, int elem, int r, cudaStream_t s)
+{
+    switch (elem) {
+    case ET_U8: return i1h_for<uint8_t, R>(a, r, s);
+    case ET_U16: return i1h_for<uint16_t, R>(a, r, s);
+    case ET_F32: return i1h_for<float, R>(a, r, s);
+    case ET_F16: return i1h_for<__half, R>(a, r, s);
+    default: return i1h_for<__nv_bfloat16, R>(a, r, s);
+    }
+}
+
+template <typename T, int R> static cudaError_t i1_for(const IterArgs &a, int r, float fp64_cond, cudaStream_t s)
+{
+    i1_iter_kernel<T, R><<<a.tiles, LK_THREADS, sizeof(float) * i1_smem_floats<R>(r, 2), s>>>(a, r, fp64_cond);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t i1_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s)
+{
+    switch (elem) {
+    case ET_U8: return i1_for<uint8_t, R>(a, r, fp64_cond, s);
+    case ET_U16: return i1_for<uint16_t, R>(a, r, fp64_cond, s);
+    case ET_F32: return i1_for<float, R>(a, r, fp64_cond, s);
+    case ET_F16: return i1_for<__half, R>(a, r, fp64_cond, s);
+    default: return i1_for<__nv_bfloat16, R>(a, r, fp64_cond, s);
+    }
+}
+
 template <int R> void *batch_kernel_ptr(int in_format, int storage)
 {
     if (in_format == OF_U8) {
@@ -137,6 +172,22 @@ template <int R> cudaError_t radius_configure()
     OF_SET((lk_iter_kernel<__half, R>));
     OF_SET((lk_iter_kernel<__nv_bfloat16, R>));
     OF_SET((window_sums_kernel<R>));
+    {
+        const int r = R == 0 ? MAX_RADIUS : R;
+        const int hb = (int)sizeof(float) * i1_smem_floats<R>(r, 3), ib = (int)sizeof(float) * i1_smem_floats<R>(r, 2);
+#define OF_SET_I1(T)                                                                                       \
+    if ((e = cudaFuncSetAttribute((const void *)i1_hess_kernel<T, R>,                                     \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess ||     \
+        (e = cudaFuncSetAttribute((const void *)i1_iter_kernel<T, R>,                                     \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ib)) != cudaSuccess)       \
+        return e;
+        OF_SET_I1(uint8_t)
+        OF_SET_I1(uint16_t)
+        OF_SET_I1(float)
+        OF_SET_I1(__half)
+        OF_SET_I1(__nv_bfloat16)
+#undef OF_SET_I1
+    }
     for (int f = 0; f < 2; ++f)
         for (int st = 0; st < 3; ++st) OF_SET(batch_kernel_ptr<R>(f, st));
 #undef OF_SET
@@ -145,6 +196,8 @@ template <int R> cudaError_t radius_configure()
 
 template cudaError_t lk_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template cudaError_t ws_launch<OF_RADIUS>(const float *, int, int, int, float *, cudaStream_t);
+template cudaError_t i1h_launch<OF_RADIUS>(const HessArgs &, int, int, cudaStream_t);
+template cudaError_t i1_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template void *batch_kernel_ptr<OF_RADIUS>(int, int);
 template cudaError_t radius_configure<OF_RADIUS>();
 template size_t radius_smem_bytes<OF_RADIUS>(int);

@@ -21,6 +21,7 @@ OF_F32, OF_F16, OF_BF16 = 0, 1, 2
 OF_FLAG_NO_GRAPH = 0x1
 OF_FLAG_STAGE_I2 = 0x2
 OF_FLAG_ZNSSD = 0x4
+OF_FLAG_I1GRAD = 0x8
 STORAGE = {"f32": OF_F32, "f16": OF_F16, "bf16": OF_BF16}
 
 

@@ -62,7 +62,7 @@ def round_bf16(a):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, perturb=0.0, seed=0, round0=False):
+def oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, perturb=0.0, seed=0, round0=False, i1grad=False):
     """The oracle's steps (FP64) on a pyramid stored as the CUDA path stores it: level 0
     exact, level l+1 = round(reduce(level l)) with round-to-nearest-even to `storage`.
     perturb > 0 multiplies each reduced value by (1 + U(-perturb, perturb)) before the
@@ -87,7 +87,8 @@ def oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, perturb=0.0, seed=0
         else:
             u, v = oracle_mod.upsample_flow(u, Hl, Wl), oracle_mod.upsample_flow(v, Hl, Wl)
         for _ in range(n):
-            u, v, _ = oracle_mod.lk_iteration(P1[l], P2[l], u, v, r)
+            it = oracle_mod.lk_iteration_i1grad if i1grad else oracle_mod.lk_iteration
+            u, v, _ = it(P1[l], P2[l], u, v, r)
     return u, v
 
 
@@ -115,14 +116,16 @@ def compare(u, v, uo, vo, mask=None):
 
 
 def parity_check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label="", margin=None, workload=True,
-                 excluded_max=None, sensitive_max=0.01, region=None, round0=False, probes=1, outliers_max=0.0):
+                 excluded_max=None, sensitive_max=0.01, region=None, round0=False, probes=1, outliers_max=0.0,
+                 i1grad=False):
     """Assert the tolerance of `storage` on the compared pixels (see the module docstring).
     workload=False (synthetic textures used for shape coverage) asserts the
-    implementation check only and reports the storage effect."""
+    implementation check only and reports the storage effect. i1grad: the variant
+    linearised with the first image's gradient, on both sides."""
     I1, I2 = images(pair_or_imgs)
     I1 = np.asarray(I1, np.float64)
     I2 = np.asarray(I2, np.float64)
-    uo, vo, q = oracle_mod.flow(I1, I2, L, r, n, want_ratio=True)
+    uo, vo, q = oracle_mod.flow(I1, I2, L, r, n, want_ratio=True, i1grad=i1grad)
     H, W = u.shape
     tmax, trms = TOL[storage]
     if margin is None:
@@ -132,7 +135,7 @@ def parity_check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label="", mar
     if region is not None:      # compare only inside `region` (the rest is reported)
         outside = ~region & ~border
         if outside.any():
-            uo_, vo_ = oracle_mod.flow(I1, I2, L, r, n)
+            uo_, vo_ = oracle_mod.flow(I1, I2, L, r, n, i1grad=i1grad)
             d = np.maximum(np.abs(u - uo_), np.abs(v - vo_))[outside]
             print(f"{label} {storage}: outside the compared region ({int(outside.sum())} px): max {d.max():.3e} "
                   f"rms {np.sqrt((d ** 2).mean()):.3e}, within tol {float((d <= TOL[storage][0]).mean()):.2%}")
@@ -141,16 +144,16 @@ def parity_check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label="", mar
     assert n_inner > 0, "no interior pixels for this margin"
     amb = ambiguous_mask(q, r, n) & ~border
     unstable = np.zeros((H, W), bool)
-    us, vs_ = oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, round0=round0)
+    us, vs_ = oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, round0=round0, i1grad=i1grad)
     for k in range(probes):
         rng = np.random.default_rng(12345 + k)
         up, vp = oracle_mod.flow(I1 * (1 + rng.uniform(-1e-6, 1e-6, I1.shape)),
-                                 I2 * (1 + rng.uniform(-1e-6, 1e-6, I2.shape)), L, r, n)
+                                 I2 * (1 + rng.uniform(-1e-6, 1e-6, I2.shape)), L, r, n, i1grad=i1grad)
         unstable |= np.maximum(np.abs(up - uo), np.abs(vp - vo)) > 0.25 * tmax
         if storage != "f32":
             # stability to a rounding flip of stored pyramid values
             uq, vq = oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, perturb=1e-6, seed=7 + k,
-                                        round0=round0)
+                                        round0=round0, i1grad=i1grad)
             unstable |= np.maximum(np.abs(uq - us), np.abs(vq - vs_)) > 0.25 * tmax
     unstable &= ~border & ~amb
     invalid = border | amb | unstable

@@ -80,3 +80,11 @@ def test_status_strings_and_version(of):
     for s in range(-7, 1):
         assert of.lib().of_status_string(s)
     assert of.version() >= 100
+
+
+def test_i1grad_flag_validates_and_adds_one_float4_per_pixel(of):
+    p = of.Plan.make(1024, 1024, bits=12, storage="f16")
+    q = of.Plan.make(1024, 1024, bits=12, storage="f16", flags=of.OF_FLAG_I1GRAD)
+    assert of.plan_validate(q) == of.OF_OK
+    assert of.workspace_bytes(q) - of.workspace_bytes(p) == 1024 * 1024 * 16
+    assert of.plan_validate(of.Plan.make(64, 64, flags=0x10)) == of.OF_EINVAL
