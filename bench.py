@@ -230,6 +230,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the single-pair and e2e legs")
+    ap.add_argument("--no-autotune", action="store_true", help="run the batched launch with the default tuning")
     ap.add_argument("--table1", action="store_true",
                     help="sweep levels {3,4} x iterations 1..7 at 1792x384, r = 10 (synthetic Table 1) and exit")
     args = ap.parse_args()
@@ -273,6 +274,12 @@ def main():
 
     def step():
         of.compute_batch(flows, I1, I2, us, vs, stream=stream)
+
+    # the library's autotuner picks how the batched launch runs (outside the timed region)
+    tuning = None
+    if not args.no_autotune:
+        from paper_1306_2461_gb300 import autotune
+        tuning = autotune.tune(flows, I1, I2, us, vs, stream=stream, reps=2, save=False)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -335,9 +342,13 @@ def main():
         "config": {"workload": WORKLOAD, "H": H, "W": W, "bits": BITS, "levels": LEVELS, "radius": RADIUS,
                    "iterations": ITERS, "pairs_per_step": B, "distinct_pairs": DISTINCT,
                    "form": "batched persistent launch (of_compute_batch), CUDA graph",
+                   "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm")}
+                              if tuning else "default (autotuner off)"),
                    "l2": "no flush: per-step working set ~%.1f GB >> 129 MB L2" % (
                        B * (of.workspace_bytes(plan16) + 4 * H * W) / 1e9),
                    "parallelism": f"replicas x{world}"},
+        "autotune_candidates_ms": ([[c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], round(c["ms"], 3)]
+                                    for c in tuning["candidates"]] if tuning else None),
         "latency_ms": {"step_p50": percentile(step_ms, 50), "step_p99": percentile(step_ms, 99),
                        "step_max": max(step_ms)},
         "mpix_iter_per_s": pixel_iterations(H, W, LEVELS, ITERS) * value / 1e6,
@@ -371,9 +382,11 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
     the target names), and e2e through the C ABI with host buffers."""
     out = {}
     K = max(args.steps, 20)
-    # plain FP32 single pair, one of_compute (graph replay) per field
-    for storage in ("f32", "f16"):
-        plan = of.Plan.make(H, W, LEVELS, RADIUS, ITERS, bits=BITS, storage=storage)
+    # plain FP32 single pair, one of_compute (graph replay) per field; the same at FP16
+    # storage, and the first-image-gradient variant (window matrix fixed per level)
+    for key, storage, flags in (("single_pair_f32", "f32", 0), ("single_pair_f16", "f16", 0),
+                                ("single_pair_f16_i1grad", "f16", of.OF_FLAG_I1GRAD)):
+        plan = of.Plan.make(H, W, LEVELS, RADIUS, ITERS, bits=BITS, storage=storage, flags=flags)
         with of.Flow(plan) as f, torch.cuda.stream(stream):
             for _ in range(5):
                 f.compute(I1[0], I2[0], us[0], vs[0], stream=stream)
@@ -386,8 +399,7 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
             stream.synchronize()
             lat = [a.elapsed_time(b) for a, b in evs]
             tot = evs[0][0].elapsed_time(evs[-1][1])
-        out[f"single_pair_{storage}"] = {"fields_per_s": K / (tot / 1000.0), "p50_ms": percentile(lat, 50),
-                                         "p99_ms": percentile(lat, 99)}
+        out[key] = {"fields_per_s": K / (tot / 1000.0), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99)}
     # e2e: host (pinned) frames in, device compute, host flow fields out, every step
     B = len(flows)
     h1 = [torch.from_numpy(src[i % len(src)].I1.astype(np.int32)).to(torch.uint16).pin_memory() for i in range(B)]

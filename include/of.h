@@ -145,6 +145,47 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
                      float *const *us, float *const *vs, of_stream_t stream);
 
 /*
+ * Autotuning of the batched launch (of_compute_batch and the serving loop). Every
+ * batch shape has the same results to within the stated tolerances whichever tuning
+ * runs it; the default tuning (no table entry) gives the results of of_compute bit for
+ * bit. A tuning:
+ *   generic_sums   1: per-output window sums of the run-time-radius kernel;
+ *                  0: grouped sums of the kernel specialised for the radius
+ *   stage_i2       1: stage I2 footprints in shared memory (specialised kernel only)
+ *   blocks_per_sm  resident blocks per SM of the persistent launch; 0 = as many as fit
+ *   ms             measured milliseconds per batch (of_autotune_batch output only)
+ * The process-wide table is keyed by the method (in_format, storage, radius, levels,
+ * iterations, OF_FLAG_ZNSSD) and a size class, round(log2(mean level-0 pixels per pair)).
+ */
+typedef struct of_tuning {
+    int32_t generic_sums;
+    int32_t stage_i2;
+    int32_t blocks_per_sm;
+    float ms;
+} of_tuning;
+
+/* Time every candidate tuning on this batch (one untimed launch, then `reps` timed
+ * launches each, CUDA events on `stream`, synchronised) and record the fastest in the
+ * table for the batch's method and size class. Arguments as of_compute_batch, except
+ * that every I1s[i] must be non-NULL (repeated launches must not move the reused
+ * pyramid) and n >= 1. The outputs hold the last candidate's fields. results (up to
+ * max_results entries, may be NULL when max_results == 0) receives each candidate's
+ * time; *n_results (may be NULL) their number; *best (may be NULL) the choice.
+ * Blocks the calling thread. OF_EINVAL, OF_ECUDA, OF_ETIMEOUT (a device wait ran out;
+ * nothing is recorded), or the errors of of_compute_batch. */
+int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
+                      float *const *us, float *const *vs, of_stream_t stream, int32_t reps, of_tuning *best,
+                      of_tuning *results, int32_t max_results, int32_t *n_results);
+/* Size class of a batch (its table key). OF_EINVAL for n < 1 or NULL handles. */
+int of_batch_size_class(int32_t n, const of_handle *hs, int32_t *size_class);
+/* Read or write one table entry (the method is a plan whose H and W are ignored).
+ * of_tuning_get: OF_ESTATE when there is no entry. of_tuning_set: OF_EINVAL for an
+ * invalid tuning (generic_sums and stage_i2 together, values out of range). Host only. */
+int of_tuning_get(const of_plan *method, int32_t size_class, of_tuning *t);
+int of_tuning_set(const of_plan *method, int32_t size_class, const of_tuning *t);
+int of_tuning_clear(void);
+
+/*
  * of_compute without any device allocation. The paper has no counterpart: this is for
  * callers that cannot call cudaMalloc once running, such as a real-time acquisition
  * loop (cudaMalloc/cudaFree can synchronise the device and stall the camera pipeline)

@@ -167,7 +167,8 @@ static int build_batch(int32_t n, const of_handle *hs, const void *const *I1s, c
     return OF_OK;
 }
 
-static void fill_header(BatchHdr &hd, const of_plan &p0, const BatchBuild &b, char *dev, size_t bar_off)
+static void fill_header(BatchHdr &hd, const of_plan &p0, const BatchBuild &b, char *dev, size_t bar_off,
+                        bool stage_i2)
 {
     const size_t pairs_bytes = sizeof(BatchPair) * b.pairs.size();
     hd.pairs = reinterpret_cast<const BatchPair *>(dev);
@@ -182,7 +183,7 @@ static void fill_header(BatchHdr &hd, const of_plan &p0, const BatchBuild &b, ch
     hd.npyr = b.npyr;
     hd.fp64_cond = p0.fp64_cond;
     hd.timeout_ns = BARRIER_TIMEOUT_NS;
-    hd.stage_i2 = (p0.flags & OF_FLAG_STAGE_I2) ? 1 : 0;
+    hd.stage_i2 = stage_i2 ? 1 : 0;
     hd.znssd = (p0.flags & OF_FLAG_ZNSSD) ? 1 : 0;
 }
 
@@ -191,17 +192,40 @@ static size_t bar_offset(const BatchBuild &b)
     return (sizeof(BatchPair) * b.pairs.size() + sizeof(int32_t) * b.prefix.size() + 255) / 256 * 256;
 }
 
-// Grid size of the persistent kernel: every block resident at once (cooperative).
-static int grid_for(void *fn, size_t smem, int device, int max_items, dim3 &grid)
+// Grid size of the persistent kernel: every block resident at once (cooperative),
+// at most blocks_per_sm per SM when that is > 0.
+static int grid_for(void *fn, size_t smem, int device, int max_items, int blocks_per_sm, dim3 &grid)
 {
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LK_THREADS, smem) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || per_sm < 1)
         return OF_ECUDA;
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
     int g = per_sm * sms;
     if (g > max_items) g = max_items > 0 ? max_items : 1;
     grid = dim3(g);
     return OF_OK;
+}
+
+// The kernel, shared memory and staging a tuning selects for a method.
+struct Resolved {
+    void *fn;
+    size_t smem;
+    bool stage;
+};
+static Resolved resolve(const of_plan &p0, const Tuning &t)
+{
+    Resolved r;
+    if (t.generic_sums) {
+        r.fn = batch_kernel_generic(p0.in_format, p0.storage);
+        r.smem = batch_smem_generic(p0.radius);
+        r.stage = false;
+    } else {
+        r.stage = (p0.flags & OF_FLAG_STAGE_I2) || t.stage_i2;
+        r.fn = batch_kernel_for(p0.in_format, p0.storage, p0.radius);
+        r.smem = batch_smem_bytes(p0.radius, r.stage);
+    }
+    return r;
 }
 
 static int commit_state(int32_t n, const of_handle *hs, const BatchBuild &b, cudaStream_t st)
@@ -264,12 +288,14 @@ int batch_run_slot(BatchSlot &slot, int32_t n, const of_handle *hs, const void *
     const size_t bar_off = bar_offset(b);
     memcpy(slot.host, b.pairs.data(), pairs_bytes);
     memcpy(slot.host + pairs_bytes, b.prefix.data(), prefix_bytes);
+    const Tuning t = tuning_for(p0, batch_size_class(n, hs));
+    const Resolved rv = resolve(p0, t);
     BatchHdr hd;
-    fill_header(hd, p0, b, slot.dev, bar_off);
-    void *fn = batch_kernel_for(p0.in_format, p0.storage, p0.radius);
-    const size_t smem = batch_smem_bytes(p0.radius);
+    fill_header(hd, p0, b, slot.dev, bar_off, rv.stage);
+    void *fn = rv.fn;
+    const size_t smem = rv.smem;
     dim3 grid;
-    if ((rc = grid_for(fn, smem, hs[0]->device, b.max_items, grid))) return rc;
+    if ((rc = grid_for(fn, smem, hs[0]->device, b.max_items, t.blocks_per_sm, grid))) return rc;
     if (cudaMemcpyAsync(slot.dev, slot.host, pairs_bytes + prefix_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(hd.barrier, 0, 2 * sizeof(unsigned int), st) != cudaSuccess)
         return OF_ECUDA;
@@ -291,24 +317,26 @@ int batch_run_slot(BatchSlot &slot, int32_t n, const of_handle *hs, const void *
 
 }  // namespace of
 
-extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
-                                float *const *us, float *const *vs, of_stream_t stream)
+namespace of {
+
+// One batched launch with an explicit tuning, through the cache of captured launches.
+int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s, float *const *us,
+              float *const *vs, cudaStream_t st, const Tuning &t)
 {
     if (n == 0) return OF_OK;
     BatchBuild b;
     int rc = build_batch(n, hs, I1s, I2s, us, vs, b);
     if (rc) return rc;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const of_plan &p0 = hs[0]->plan;
     const size_t pairs_bytes = sizeof(BatchPair) * n, prefix_bytes = sizeof(int32_t) * b.prefix.size();
-    std::vector<char> key(pairs_bytes + prefix_bytes + sizeof(st) + 3 * sizeof(int));
+    std::vector<char> key(pairs_bytes + prefix_bytes + sizeof(st) + 6 * sizeof(int));
     {
         char *k = key.data();
         memcpy(k, b.pairs.data(), pairs_bytes);
         memcpy(k + pairs_bytes, b.prefix.data(), prefix_bytes);
         memcpy(k + pairs_bytes + prefix_bytes, &st, sizeof(st));
-        const int extra[3] = {p0.radius, (int)(p0.iterations * 8 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD))),
-                              hs[0]->device};
+        const int extra[6] = {p0.radius, (int)(p0.iterations * 8 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD))),
+                              hs[0]->device, t.generic_sums, t.stage_i2, t.blocks_per_sm};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
 
@@ -340,10 +368,11 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
             release(ne);
             return OF_ECUDA;
         }
-        fill_header(ne.hdr, p0, b, ne.dev, bar_off);
-        ne.fn = batch_kernel_for(p0.in_format, p0.storage, p0.radius);
-        ne.smem = batch_smem_bytes(p0.radius);
-        if ((rc = grid_for(ne.fn, ne.smem, ne.device, b.max_items, ne.grid))) {
+        const Resolved rv = resolve(p0, t);
+        fill_header(ne.hdr, p0, b, ne.dev, bar_off, rv.stage);
+        ne.fn = rv.fn;
+        ne.smem = rv.smem;
+        if ((rc = grid_for(ne.fn, ne.smem, ne.device, b.max_items, t.blocks_per_sm, ne.grid))) {
             release(ne);
             return rc;
         }
@@ -370,4 +399,15 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
     if (err != cudaSuccess) return OF_ECUDA;
     if (cudaEventRecord(e->done, st) != cudaSuccess) return OF_ECUDA;
     return commit_state(n, hs, b, st);
+}
+
+}  // namespace of
+
+extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
+                                float *const *us, float *const *vs, of_stream_t stream)
+{
+    if (n <= 0) return n == 0 ? OF_OK : OF_EINVAL;
+    if (!hs || !hs[0]) return OF_EINVAL;
+    const Tuning t = tuning_for(hs[0]->plan, batch_size_class(n, hs));
+    return run_batch(n, hs, I1s, I2s, us, vs, reinterpret_cast<cudaStream_t>(stream), t);
 }

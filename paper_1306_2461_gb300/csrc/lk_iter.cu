@@ -56,14 +56,17 @@ void *batch_kernel_for(int in_format, int storage, int radius)
 }
 
 #define OF_CASE_SM(R) \
-    case R: return radius_smem_bytes<R>(radius);
-size_t batch_smem_bytes(int radius)
+    case R: return radius_smem_bytes<R>(radius, stage_i2);
+size_t batch_smem_bytes(int radius, bool stage_i2)
 {
     switch (radius) {
         OF_RADII(OF_CASE_SM)
-    default: return radius_smem_bytes<0>(radius);
+    default: return radius_smem_bytes<0>(radius, stage_i2);
     }
 }
+
+void *batch_kernel_generic(int in_format, int storage) { return batch_kernel_ptr<0>(in_format, storage); }
+size_t batch_smem_generic(int radius) { return radius_smem_bytes<0>(radius, false); }
 
 #define OF_CFG(R) \
     if ((e = radius_configure<R>()) != cudaSuccess) return e;

@@ -70,6 +70,19 @@ void drop_graphs(of_ctx *h);
 // cudaMalloc that honours of_debug_fail_allocs (injected out-of-memory failures).
 cudaError_t dev_malloc(void **p, size_t bytes);
 
+// How one persistent batched launch is run (the autotuner's choice; see tune.cu).
+struct Tuning {
+    int generic_sums = 0;    // 1: the run-time-radius kernel (per-output sums); 0: grouped fixed-radius sums
+    int stage_i2 = 0;        // 1: stage I2 footprints in shared memory (fixed-radius kernel only)
+    int blocks_per_sm = 0;   // resident blocks per SM; 0 = as many as fit
+};
+// The tuning table entry for this method and size class, or the default.
+Tuning tuning_for(const of_plan &method, int size_class);
+// round(log2(mean level-0 pixels per pair)) of a batch.
+int batch_size_class(int32_t n, const of_handle *hs);
+int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s, float *const *us,
+              float *const *vs, cudaStream_t st, const Tuning &t);
+
 struct BatchSlot {
     char *dev = nullptr;
     char *host = nullptr;

@@ -120,7 +120,10 @@ constexpr int ZN_EPS = 1;             // added to the local variance (counts squ
 
 // Tile shapes.
 constexpr int LK_TW = 64;    // iteration output tile width
-constexpr int LK_TH = 32;    // iteration output tile height
+#ifndef OF_LK_TH
+#define OF_LK_TH 32
+#endif
+constexpr int LK_TH = OF_LK_TH;   // iteration output tile height (a multiple of 4)
 #ifndef OF_LK_THREADS
 #define OF_LK_THREADS 256
 #endif
@@ -128,7 +131,10 @@ constexpr int LK_THREADS = OF_LK_THREADS;   // threads per iteration / batch blo
 constexpr int PYR_TW = 32;   // pyramid output tile
 constexpr int PYR_TH = 16;
 constexpr int PYR_THREADS = 256;
-constexpr int MAX_RADIUS = 16;
+#ifndef OF_MAX_RADIUS
+#define OF_MAX_RADIUS 16
+#endif
+constexpr int MAX_RADIUS = OF_MAX_RADIUS;
 
 // Window radii with a kernel specialised at compile time (the workloads' and the
 // paper's radii); any other radius runs the generic kernel.
@@ -146,7 +152,9 @@ cudaError_t launch_window_sums(const float *ch, int H, int W, int r, float *out,
 cudaError_t launch_i1_hess(const HessArgs &a, int elem, int radius, cudaStream_t s);
 cudaError_t launch_i1_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s);
 void *batch_kernel_for(int in_format, int storage, int radius);
-size_t batch_smem_bytes(int radius);
+size_t batch_smem_bytes(int radius, bool stage_i2);
+void *batch_kernel_generic(int in_format, int storage);   // the run-time-radius kernel
+size_t batch_smem_generic(int radius);
 cudaError_t launch_level_to_f32(const Level &l, int elem, float *dst, cudaStream_t s);
 cudaError_t launch_wait_timeout(int *flag, int *status, long long timeout_ns, cudaStream_t s);
 cudaError_t configure_lk_kernels();   // all kernels with dynamic shared memory, current device
@@ -158,6 +166,6 @@ template <int R> cudaError_t i1h_launch(const HessArgs &a, int elem, int r, cuda
 template <int R> cudaError_t i1_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> void *batch_kernel_ptr(int in_format, int storage);
 template <int R> cudaError_t radius_configure();
-template <int R> size_t radius_smem_bytes(int r);
+template <int R> size_t radius_smem_bytes(int r, bool stage_i2);
 
 }  // namespace of

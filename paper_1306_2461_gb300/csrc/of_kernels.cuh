@@ -381,10 +381,12 @@ template <int R> struct FixedTile {
     // I2 staged in shared memory as FP32: the bounding box of every tap the region's
     // warps read, when it holds at most FBOX floats (else the taps come from global).
     static constexpr int FBOX = (RW + 10) * (RH + 10);
-    static constexpr int OFF_FBOX = 5 * PLANE;
-    static constexpr int OFF_BAR = (OFF_FBOX + FBOX + 1) / 2 * 2;   // 8-byte aligned mbarrier
+    static_assert(PLANE % 2 == 0, "the mbarrier after the planes must be 8-byte aligned");
+    static constexpr int OFF_BAR = 5 * PLANE;                        // 8-byte aligned mbarrier
     static constexpr int OFF_BOX = OFF_BAR + 2;                      // 4 ints: box bounds
-    static constexpr int SMEM_FLOATS = OFF_BOX + 4;
+    static constexpr int OFF_FBOX = OFF_BOX + 4;
+    static constexpr int SMEM_NOSTAGE = OFF_FBOX;                    // launches without I2 staging
+    static constexpr int SMEM_FLOATS = OFF_FBOX + FBOX;
 #ifndef OF_LK_MIN_BLOCKS
 #define OF_LK_MIN_BLOCKS 3
 #endif
@@ -715,10 +717,10 @@ template <int R> constexpr int batch_min_blocks()
     return m < OF_BATCH_MIN_BLOCKS ? m : OF_BATCH_MIN_BLOCKS;
 }
 
-template <int R> inline __host__ __device__ int lk_tile_smem_floats(int r)
+template <int R> inline __host__ __device__ int lk_tile_smem_floats(int r, bool stage_i2)
 {
     if constexpr (R == 0) return lk_smem_floats(r);
-    else return FixedTile<R>::SMEM_FLOATS;
+    else return stage_i2 ? FixedTile<R>::SMEM_FLOATS : FixedTile<R>::SMEM_NOSTAGE;
 }
 
 }  // namespace of

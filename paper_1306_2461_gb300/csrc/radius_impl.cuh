@@ -80,9 +80,9 @@ window_sums_kernel(const float *ch, int H, int W, int r, int tiles_x, float *out
     }
 }
 
-template <int R> size_t radius_smem_bytes(int r)
+template <int R> size_t radius_smem_bytes(int r, bool stage_i2)
 {
-    const size_t lk = sizeof(float) * (size_t)lk_tile_smem_floats<R>(r);
+    const size_t lk = sizeof(float) * (size_t)lk_tile_smem_floats<R>(r, stage_i2);
     size_t pyr = sizeof(float) * (size_t)PYR_SMEM_FLOATS;
     const size_t zn = sizeof(float) * (size_t)ZN_SMEM_FLOATS;
     if (zn > pyr) pyr = zn;
@@ -91,7 +91,8 @@ template <int R> size_t radius_smem_bytes(int r)
 
 template <typename T, int R> static cudaError_t lk_for(const IterArgs &a, int r, float fp64_cond, cudaStream_t s)
 {
-    lk_iter_kernel<T, R><<<a.tiles, LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r), s>>>(a, r, fp64_cond);
+    lk_iter_kernel<T, R><<<a.tiles, LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r, a.stage_i2 != 0), s>>>(
+        a, r, fp64_cond);
     return cudaGetLastError();
 }
 
@@ -109,7 +110,7 @@ template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float
 template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, float *out, cudaStream_t s)
 {
     const int tiles_x = (W + LK_TW - 1) / LK_TW, tiles_y = (H + LK_TH - 1) / LK_TH;
-    window_sums_kernel<R><<<tiles_x * tiles_y, LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r), s>>>(
+    window_sums_kernel<R><<<tiles_x * tiles_y, LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r, false), s>>>(
         ch, H, W, r, tiles_x, out);
     return cudaGetLastError();
 }
@@ -163,7 +164,7 @@ template <int R> void *batch_kernel_ptr(int in_format, int storage)
 // Raise the dynamic shared memory limit of this radius's kernels on the current device.
 template <int R> cudaError_t radius_configure()
 {
-    const int bytes = (int)radius_smem_bytes<R>(R == 0 ? MAX_RADIUS : R);
+    const int bytes = (int)radius_smem_bytes<R>(R == 0 ? MAX_RADIUS : R, true);
     cudaError_t e;
 #define OF_SET(fn) if ((e = cudaFuncSetAttribute((const void *)(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e
     OF_SET((lk_iter_kernel<uint8_t, R>));
@@ -200,6 +201,6 @@ template cudaError_t i1h_launch<OF_RADIUS>(const HessArgs &, int, int, cudaStrea
 template cudaError_t i1_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template void *batch_kernel_ptr<OF_RADIUS>(int, int);
 template cudaError_t radius_configure<OF_RADIUS>();
-template size_t radius_smem_bytes<OF_RADIUS>(int);
+template size_t radius_smem_bytes<OF_RADIUS>(int, bool);
 
 }  // namespace of

@@ -1,0 +1,189 @@
+// The autotuner of the persistent batched launch. A process-wide table maps a method
+// (input format, storage, radius, levels, iterations, normalisation) and a size class
+// (round(log2(mean level-0 pixels per pair))) to a Tuning: window-sum strategy, I2
+// staging and resident blocks per SM. of_compute_batch and the serving loop read it;
+// of_autotune_batch fills it by timing every candidate on the caller's own batch.
+#include <math.h>
+#include <string.h>
+
+#include <array>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "of_engine.h"
+#include "of_internal.cuh"
+
+namespace of {
+
+namespace {
+
+using Key = std::array<int, 7>;
+
+std::mutex g_tune_mu;
+std::map<Key, Tuning> g_table;
+
+Key key_of(const of_plan &m, int size_class)
+{
+    return {m.in_format, m.storage, m.radius, m.levels, m.iterations, (m.flags & OF_FLAG_ZNSSD) ? 1 : 0, size_class};
+}
+
+bool radius_is_specialised(int r)
+{
+#define OF_IS(R) if (r == R) return true;
+    OF_RADII(OF_IS)
+#undef OF_IS
+    return false;
+}
+
+bool valid(const Tuning &t) { return t.generic_sums >= 0 && t.generic_sums <= 1 && t.stage_i2 >= 0 && t.stage_i2 <= 1 &&
+                                     t.blocks_per_sm >= 0 && t.blocks_per_sm <= 64 && !(t.generic_sums && t.stage_i2); }
+
+}  // namespace
+
+Tuning tuning_for(const of_plan &method, int size_class)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_table.find(key_of(method, size_class));
+    return it == g_table.end() ? Tuning() : it->second;
+}
+
+int batch_size_class(int32_t n, const of_handle *hs)
+{
+    double px = 0.0;
+    int m = 0;
+    for (int i = 0; i < n; ++i)
+        if (hs[i]) {
+            px += (double)hs[i]->lay.H[0] * hs[i]->lay.W[0];
+            ++m;
+        }
+    return m ? (int)lround(log2(px / m)) : 0;
+}
+
+}  // namespace of
+
+using namespace of;
+
+extern "C" {
+
+int of_batch_size_class(int32_t n, const of_handle *hs, int32_t *size_class)
+{
+    if (n < 1 || !hs || !size_class) return OF_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!hs[i]) return OF_EINVAL;
+    *size_class = batch_size_class(n, hs);
+    return OF_OK;
+}
+
+int of_tuning_get(const of_plan *method, int32_t size_class, of_tuning *t)
+{
+    if (of_plan_validate(method) != OF_OK || !t) return OF_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_table.find(key_of(*method, size_class));
+    if (it == g_table.end()) return OF_ESTATE;
+    t->generic_sums = it->second.generic_sums;
+    t->stage_i2 = it->second.stage_i2;
+    t->blocks_per_sm = it->second.blocks_per_sm;
+    t->ms = 0.0f;
+    return OF_OK;
+}
+
+int of_tuning_set(const of_plan *method, int32_t size_class, const of_tuning *t)
+{
+    if (of_plan_validate(method) != OF_OK || !t) return OF_EINVAL;
+    Tuning v;
+    v.generic_sums = t->generic_sums;
+    v.stage_i2 = t->stage_i2;
+    v.blocks_per_sm = t->blocks_per_sm;
+    if (!valid(v)) return OF_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_table[key_of(*method, size_class)] = v;
+    return OF_OK;
+}
+
+int of_tuning_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_table.clear();
+    return OF_OK;
+}
+
+int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
+                      float *const *us, float *const *vs, of_stream_t stream, int32_t reps, of_tuning *best,
+                      of_tuning *results, int32_t max_results, int32_t *n_results)
+{
+    if (n < 1 || !hs || !I1s || reps < 1 || reps > 1000 || max_results < 0 || (max_results > 0 && !results))
+        return OF_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!hs[i] || !I1s[i]) return OF_EINVAL;   // repeated runs must not change which pyramid is reused
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const of_plan &p0 = hs[0]->plan;
+    // candidates: the grouped fixed-radius sums (gathered or staged I2) when the radius
+    // has a specialised kernel, the per-output sums of the run-time-radius kernel, each
+    // at full occupancy and at 1 and 2 blocks per SM
+    std::vector<Tuning> cand;
+    const int occ[3] = {0, 2, 1};
+    for (int gs = radius_is_specialised(p0.radius) ? 0 : 1; gs <= 1; ++gs)
+        for (int sg = 0; sg <= (gs ? 0 : 1); ++sg)
+            for (int b : occ) {
+                Tuning t;
+                t.generic_sums = gs;
+                t.stage_i2 = sg;
+                t.blocks_per_sm = b;
+                cand.push_back(t);
+            }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return OF_ECUDA;
+    }
+    int rc = OF_OK, nres = 0, ibest = -1;
+    float best_ms = 0.0f;
+    for (size_t c = 0; c < cand.size() && rc == OF_OK; ++c) {
+        // one untimed launch (captures the graph), then reps timed launches
+        if ((rc = run_batch(n, hs, I1s, I2s, us, vs, st, cand[c])) != OF_OK) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = OF_ECUDA; break; }
+        for (int k = 0; k < reps && rc == OF_OK; ++k) rc = run_batch(n, hs, I1s, I2s, us, vs, st, cand[c]);
+        if (rc != OF_OK) break;
+        float ms = 0.0f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = OF_ECUDA;
+            break;
+        }
+        ms /= (float)reps;
+        for (int i = 0; i < n; ++i) {   // a device-side failure (a timed-out wait) disqualifies the run
+            const int s = of_sync_status(hs[i]);
+            if (s != OF_OK) rc = s;
+        }
+        if (rc != OF_OK) break;
+        if (nres < max_results) {
+            results[nres].generic_sums = cand[c].generic_sums;
+            results[nres].stage_i2 = cand[c].stage_i2;
+            results[nres].blocks_per_sm = cand[c].blocks_per_sm;
+            results[nres].ms = ms;
+            ++nres;
+        }
+        if (ibest < 0 || ms < best_ms) {
+            ibest = (int)c;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_results) *n_results = nres;
+    if (rc != OF_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_table[key_of(p0, batch_size_class(n, hs))] = cand[ibest];
+    }
+    if (best) {
+        best->generic_sums = cand[ibest].generic_sums;
+        best->stage_i2 = cand[ibest].stage_i2;
+        best->blocks_per_sm = cand[ibest].blocks_per_sm;
+        best->ms = best_ms;
+    }
+    return OF_OK;
+}
+
+}  // extern "C"

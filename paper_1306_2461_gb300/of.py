@@ -55,6 +55,15 @@ class Plan(ctypes.Structure):
                 f"storage={self.storage}, fp64_cond={self.fp64_cond}, flags={self.flags})")
 
 
+class Tuning(ctypes.Structure):
+    """of_tuning: how a batched launch runs (see include/of.h)."""
+    _fields_ = [("generic_sums", ctypes.c_int32), ("stage_i2", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1306_2461_gb300.build` "
@@ -79,6 +88,12 @@ def _load():
         "of_sbubble_count": (ctypes.c_int, [vp, i32, i32, ctypes.c_float, vp, vp]),
         "of_field_minmax": (ctypes.c_int, [vp, i32, i32, vp, vp]),
         "of_debug_fail_allocs": (ctypes.c_int, [i32]),
+        "of_autotune_batch": (ctypes.c_int, [i32, pp, pp, pp, pp, pp, vp, i32, ctypes.POINTER(Tuning),
+                                             ctypes.POINTER(Tuning), i32, ctypes.POINTER(i32)]),
+        "of_batch_size_class": (ctypes.c_int, [i32, pp, ctypes.POINTER(i32)]),
+        "of_tuning_get": (ctypes.c_int, [P, i32, ctypes.POINTER(Tuning)]),
+        "of_tuning_set": (ctypes.c_int, [P, i32, ctypes.POINTER(Tuning)]),
+        "of_tuning_clear": (ctypes.c_int, []),
         "of_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "of_version": (ctypes.c_int, []),
     }
@@ -224,13 +239,59 @@ def compute_batch(flows, I1s, I2s, us=None, vs=None, stream=None):
         us = [torch.empty((f.plan.H, f.plan.W), dtype=torch.float32, device="cuda") for f in flows]
     if vs is None:
         vs = [torch.empty((f.plan.H, f.plan.W), dtype=torch.float32, device="cuda") for f in flows]
+    _check(_lib.of_compute_batch(n, *_batch_ptrs(flows, I1s, I2s, us, vs), _stream(stream)), "of_compute_batch")
+    return us, vs
+
+
+def _batch_ptrs(flows, I1s, I2s, us, vs):
+    n = len(flows)
     hs = _ptr_array([f.handle.value for f in flows])
     a1 = _ptr_array([_img_ptr(I1s[i], flows[i].plan, "I1") for i in range(n)])
     a2 = _ptr_array([_img_ptr(I2s[i], flows[i].plan, "I2") for i in range(n)])
     au = _ptr_array([_flow_ptr(us[i], flows[i].plan, "u") for i in range(n)])
     av = _ptr_array([_flow_ptr(vs[i], flows[i].plan, "v") for i in range(n)])
-    _check(_lib.of_compute_batch(n, hs, a1, a2, au, av, _stream(stream)), "of_compute_batch")
-    return us, vs
+    return hs, a1, a2, au, av
+
+
+def autotune_batch(flows, I1s, I2s, us=None, vs=None, stream=None, reps=3):
+    """of_autotune_batch: time every candidate tuning on this batch and record the
+    fastest in the library's table. Returns (best, [each candidate]) as dicts."""
+    n = len(flows)
+    if us is None:
+        us = [torch.empty((f.plan.H, f.plan.W), dtype=torch.float32, device="cuda") for f in flows]
+    if vs is None:
+        vs = [torch.empty((f.plan.H, f.plan.W), dtype=torch.float32, device="cuda") for f in flows]
+    best = Tuning()
+    res = (Tuning * 32)()
+    nres = ctypes.c_int32()
+    _check(_lib.of_autotune_batch(n, *_batch_ptrs(flows, I1s, I2s, us, vs), _stream(stream), int(reps),
+                                  ctypes.byref(best), res, len(res), ctypes.byref(nres)), "of_autotune_batch")
+    return best.as_dict(), [res[i].as_dict() for i in range(nres.value)]
+
+
+def batch_size_class(flows) -> int:
+    sc = ctypes.c_int32()
+    _check(_lib.of_batch_size_class(len(flows), _ptr_array([f.handle.value for f in flows]), ctypes.byref(sc)),
+           "of_batch_size_class")
+    return sc.value
+
+
+def tuning_get(method: Plan, size_class: int) -> dict | None:
+    t = Tuning()
+    rc = _lib.of_tuning_get(ctypes.byref(method), int(size_class), ctypes.byref(t))
+    if rc == OF_ESTATE:
+        return None
+    _check(rc, "of_tuning_get")
+    return t.as_dict()
+
+
+def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=0, blocks_per_sm=0):
+    t = Tuning(int(generic_sums), int(stage_i2), int(blocks_per_sm), 0.0)
+    _check(_lib.of_tuning_set(ctypes.byref(method), int(size_class), ctypes.byref(t)), "of_tuning_set")
+
+
+def tuning_clear():
+    _check(_lib.of_tuning_clear(), "of_tuning_clear")
 
 
 def window_sums(ch: torch.Tensor, r: int, stream=None) -> torch.Tensor:

@@ -88,3 +88,20 @@ def test_i1grad_flag_validates_and_adds_one_float4_per_pixel(of):
     assert of.plan_validate(q) == of.OF_OK
     assert of.workspace_bytes(q) - of.workspace_bytes(p) == 1024 * 1024 * 16
     assert of.plan_validate(of.Plan.make(64, 64, flags=0x10)) == of.OF_EINVAL
+
+
+def test_tuning_table_host_calls(of):
+    m = of.Plan.make(64, 64, 3, 4, 5, bits=12, storage="f16")
+    of.tuning_clear()
+    assert of.tuning_get(m, 20) is None
+    of.tuning_set(m, 20, generic_sums=0, stage_i2=1, blocks_per_sm=2)
+    t = of.tuning_get(m, 20)
+    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"]) == (0, 1, 2)
+    assert of.tuning_get(m, 19) is None                                   # another size class
+    assert of.tuning_get(of.Plan.make(64, 64, 3, 4, 4, bits=12, storage="f16"), 20) is None   # another method
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, generic_sums=1, stage_i2=1)                  # staging needs the grouped kernel
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, blocks_per_sm=-1)
+    of.tuning_clear()
+    assert of.tuning_get(m, 20) is None
