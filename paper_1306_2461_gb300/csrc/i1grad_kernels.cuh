@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(LK_THREADS, 4) i1_iter_kernel(IterArgs a, int 
                 float c, gx, gy;
                 i1_grad<true>(I1, a.pitch, a.H, a.W, x, y, c, gx, gy);
                 const float Iw = bil<true>(I2, a.pitch, a.H, a.W, (float)x + f[k].x, (float)y + f[k].y);
-                const float e = c - Iw + gx * (f[k].x - ref.x) + gy * (f[k].y - ref.y);
+                const float e = resid(c, Iw, gx, gy, f[k].x - ref.x, f[k].y - ref.y);
                 p0 = gx * e;
                 p1 = gy * e;
             }

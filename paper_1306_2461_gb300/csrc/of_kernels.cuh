@@ -39,6 +39,12 @@ constexpr int PYR_RH = 2 * PYR_TH + 3;
 constexpr int PYR_RW = 2 * PYR_TW + 3;
 constexpr int PYR_SMEM_FLOATS = PYR_RH * PYR_RW + PYR_RH * PYR_TW;
 
+// [1 4 6 4 1] . (a, b, c, d, e), with its roundings fixed: (a + e) + 4 (b + d) + 6 c.
+__device__ __forceinline__ float binom5(float a, float b, float c, float d, float e)
+{
+    return fmaf(6.0f, c, fmaf(4.0f, __fadd_rn(b, d), __fadd_rn(a, e)));
+}
+
 // One output tile (PYR_TH x PYR_TW at level l+1) of image `img` (0/1) of a pair.
 // FIRST: the source is the raw camera image; level 0 is stored as well, unchanged in
 // the camera's integer format.
@@ -72,7 +78,7 @@ __device__ __forceinline__ void pyr_tile_smem(const PyrArgs &a, int tile, int im
     for (int i = threadIdx.x; i < PYR_RH * PYR_TW; i += blockDim.x) {
         const int r = i / PYR_TW, j = i - r * PYR_TW;
         const float *q = s_in + r * PYR_RW + 2 * j;
-        s_h[i] = q[0] + 4.0f * q[1] + 6.0f * q[2] + 4.0f * q[3] + q[4];
+        s_h[i] = binom5(q[0], q[1], q[2], q[3], q[4]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < PYR_TH * PYR_TW; i += blockDim.x) {
@@ -80,7 +86,7 @@ __device__ __forceinline__ void pyr_tile_smem(const PyrArgs &a, int tile, int im
         const int y = ty0 + r, x = tx0 + j;
         if (y < a.Ho && x < a.Wo) {
             const float *q = s_h + 2 * r * PYR_TW + j;
-            const float s = q[0] + 4.0f * q[PYR_TW] + 6.0f * q[2 * PYR_TW] + 4.0f * q[3 * PYR_TW] + q[4 * PYR_TW];
+            const float s = binom5(q[0], q[PYR_TW], q[2 * PYR_TW], q[3 * PYR_TW], q[4 * PYR_TW]);
             d[(size_t)y * a.dst_pitch + x] = to_elem<Tout>(s * (1.0f / 256.0f));
         }
     }
@@ -153,7 +159,16 @@ __device__ __forceinline__ void znssd_tile(const ZnArgs &a, int tile, int img, f
 }
 
 // ------------------------------------------------------------ iteration helpers
-__device__ __forceinline__ float lerpf(float p, float q, float t) { return (1.0f - t) * p + t * q; }
+// The arithmetic below is written with explicit fused and unfused operations so that
+// every code path that computes a quantity (per-pair and batched kernels, gathered and
+// staged taps) rounds it the same way, whatever the compiler would contract.
+__device__ __forceinline__ float lerpf(float p, float q, float t) { return fmaf(t, q, __fmul_rn(1.0f - t, p)); }
+
+// e~ = I1 - I2w + gx dx + gy dy (dx, dy: current estimate minus the tile's reference).
+__device__ __forceinline__ float resid(float i1, float Iw, float gx, float gy, float dx, float dy)
+{
+    return fmaf(gy, dy, fmaf(gx, dx, __fsub_rn(i1, Iw)));
+}
 
 // Bilinear sample with the position clamped to [0, W-1] x [0, H-1].
 template <bool NC, typename T>
@@ -275,7 +290,7 @@ __device__ __forceinline__ bool solve2(const float s[5], float fp64_cond, float 
     const float a = s[0], b = s[1], c = s[2], d = s[3], e = s[4];
     const float tr = a + c;
     if (!(tr > 0.0f)) return false;
-    const float det = fmaf(a, c, -(b * b));
+    const float det = fmaf(a, c, -__fmul_rn(b, b));
     if (fp64_cond > 0.0f && !(det * fp64_cond > tr * tr)) {
         const double A = a, B = b, C = c, D = d, E = e;
         const double T = A + C, dt = A * C - B * B;
@@ -286,8 +301,8 @@ __device__ __forceinline__ bool solve2(const float s[5], float fp64_cond, float 
     }
     if (!(det > 1e-6f * tr * tr)) return false;
     const float inv = __fdividef(1.0f, det);   // det < 2^126 for any sums of 16-bit data
-    xu = (c * d - b * e) * inv;
-    xv = (a * e - b * d) * inv;
+    xu = fmaf(c, d, -__fmul_rn(b, e)) * inv;
+    xv = fmaf(a, e, -__fmul_rn(b, d)) * inv;
     return true;
 }
 
@@ -326,7 +341,7 @@ __device__ __forceinline__ void lk_tile_generic(const IterArgs &a, int tile, int
             const float2 f = flow_at<NC>(a, x, y);
             float Iw, gx, gy;
             sample_grad<NC>(I2, a.pitch, a.H, a.W, (float)x + f.x, (float)y + f.y, Iw, gx, gy);
-            const float e = ldf<NC>(I1 + (size_t)y * a.pitch + x) - Iw + gx * (f.x - ref.x) + gy * (f.y - ref.y);
+            const float e = resid(ldf<NC>(I1 + (size_t)y * a.pitch + x), Iw, gx, gy, f.x - ref.x, f.y - ref.y);
             p0 = gx * gx;
             p1 = gx * gy;
             p2 = gy * gy;
@@ -459,6 +474,7 @@ __device__ __forceinline__ void box_h_inplace(float *P)
 {
     using F = FixedTile<R>;
     constexpr int NG = LK_TW / 4;
+    static_assert(32 % NG == 0 && LK_THREADS % 32 == 0, "a row's items must lie in one warp");
     constexpr int NITEMS = F::RH * NG;
     constexpr int IT = (NITEMS + LK_THREADS - 1) / LK_THREADS;
 #pragma unroll 1
@@ -485,7 +501,9 @@ __device__ __forceinline__ void box_h_inplace(float *P)
                 res[k] = make_float4(o[0], o[1], o[2], o[3]);
             }
         }
-        __syncthreads();   // every read of plane c is done before it is overwritten
+        // Item i covers row i / NG: the NG = 16 items of a row are 16 consecutive lanes
+        // of one warp (in every pass), so only that warp reads what it overwrites.
+        __syncwarp();
 #pragma unroll
         for (int k = 0; k < IT; ++k) {
             const int i = threadIdx.x + k * LK_THREADS;
@@ -637,8 +655,7 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
                     sample_grad_box(fbox, bw, bx0, by0, a.H, a.W, (float)x + f[u].x, (float)y + f[u].y, Iw, gx, gy);
                 else
                     sample_grad<NC>(I2, a.pitch, a.H, a.W, (float)x + f[u].x, (float)y + f[u].y, Iw, gx, gy);
-                const float e =
-                    ldf<NC>(I1 + (y * a.pitch + x)) - Iw + gx * (f[u].x - ref.x) + gy * (f[u].y - ref.y);
+                const float e = resid(ldf<NC>(I1 + (y * a.pitch + x)), Iw, gx, gy, f[u].x - ref.x, f[u].y - ref.y);
                 p0 = gx * gx;
                 p1 = gx * gy;
                 p2 = gy * gy;
