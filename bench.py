@@ -399,7 +399,14 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
             stream.synchronize()
             lat = [a.elapsed_time(b) for a, b in evs]
             tot = evs[0][0].elapsed_time(evs[-1][1])
-        out[key] = {"fields_per_s": K / (tot / 1000.0), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99)}
+            # accuracy of this form on the first pair (outside the timed region)
+            f.compute(I1[0], I2[0], us[0], vs[0], stream=stream)
+            stream.synchronize()
+        m = (RADIUS + 2) * 2 ** (LEVELS - 1)
+        e = np.sqrt((us[0].cpu().double().numpy() - src[0].u_gt) ** 2 +
+                    (vs[0].cpu().double().numpy() - src[0].v_gt) ** 2)[m:-m, m:-m]
+        out[key] = {"fields_per_s": K / (tot / 1000.0), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+                    "epe_vs_ground_truth_px": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}}
     # e2e: host (pinned) frames in, device compute, host flow fields out, every step
     B = len(flows)
     h1 = [torch.from_numpy(src[i % len(src)].I1.astype(np.int32)).to(torch.uint16).pin_memory() for i in range(B)]
