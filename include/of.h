@@ -145,6 +145,23 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
                      float *const *us, float *const *vs, of_stream_t stream);
 
 /*
+ * of_compute_batch from and to HOST buffers, with the copies overlapped with the
+ * computation. The pairs are taken in chunks of `chunk` pairs (0: four chunks): chunk
+ * k's frames are uploaded (hI1s/hI2s -> dI1s/dI2s) on an internal stream, its
+ * persistent launch runs on `stream` after that upload, and its fields are downloaded
+ * (dus/dvs -> hus/hvs) on a second internal stream after the launch, so the uploads
+ * and downloads of neighbouring chunks overlap the launches. hI1s[i] == NULL reuses
+ * the previous pyramid (dI1s[i] is then ignored). Host buffers should be pinned (page-
+ * locked) for the copies to be asynchronous; device buffers are caller-owned, sized
+ * as in of_compute. The call is complete (fields in hus/hvs) when `stream` reaches it.
+ * Errors as of_compute_batch; an error after the first chunk was queued leaves the
+ * earlier chunks queued.
+ */
+int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1s, const void *const *hI2s,
+                          float *const *hus, float *const *hvs, void *const *dI1s, void *const *dI2s,
+                          float *const *dus, float *const *dvs, of_stream_t stream, int32_t chunk);
+
+/*
  * Autotuning of the batched launch (of_compute_batch and the serving loop). Every
  * batch shape has the same results to within the stated tolerances whichever tuning
  * runs it; the default tuning (no table entry) gives the results of of_compute bit for

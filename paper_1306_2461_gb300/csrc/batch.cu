@@ -4,6 +4,7 @@
 // caches the captured launches and records the handles' state.
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -410,4 +411,94 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
     if (!hs || !hs[0]) return OF_EINVAL;
     const Tuning t = tuning_for(hs[0]->plan, batch_size_class(n, hs));
     return run_batch(n, hs, I1s, I2s, us, vs, reinterpret_cast<cudaStream_t>(stream), t);
+}
+
+// ------------------------------------------------------ host-buffer pipelined form
+// of_compute_batch_host: the batch in chunks; chunk k's upload runs on a copy stream,
+// its persistent launch on the caller's stream after that upload, and its download on a
+// second copy stream after the launch, so that uploads, launches and downloads of
+// neighbouring chunks overlap. Events order the three streams; the caller's stream
+// waits for the last download before the call's completion.
+namespace {
+
+struct HostPipe {
+    cudaStream_t up = nullptr, down = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~HostPipe()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);   // released once recorded work completes
+        if (up) cudaStreamDestroy(up);    // likewise: pending copies still run
+        if (down) cudaStreamDestroy(down);
+    }
+    cudaEvent_t make()
+    {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        ev.push_back(e);
+        return e;
+    }
+};
+
+}  // namespace
+
+extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1s, const void *const *hI2s,
+                                     float *const *hus, float *const *hvs, void *const *dI1s, void *const *dI2s,
+                                     float *const *dus, float *const *dvs, of_stream_t stream, int32_t chunk)
+{
+    if (n == 0) return OF_OK;
+    if (n < 0 || n > 65536 || !hs || !hI1s || !hI2s || !hus || !hvs || !dI1s || !dI2s || !dus || !dvs || chunk < 0)
+        return OF_EINVAL;
+    std::vector<of_handle> seen(hs, hs + n);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return OF_EINVAL;   // a handle twice
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || !hI2s[i] || !hus[i] || !hvs[i] || !dI2s[i] || !dus[i] || !dvs[i] || (hI1s[i] && !dI1s[i]))
+            return OF_EINVAL;
+        if (!same_method(hs[i]->plan, hs[0]->plan) || (hs[i]->plan.flags & OF_FLAG_I1GRAD) ||
+            hs[i]->device != hs[0]->device)
+            return OF_EINVAL;
+        if (!hI1s[i] && !hs[i]->has_prev) return OF_ESTATE;
+    }
+    const int per = chunk > 0 ? chunk : (n + 3) / 4;
+    const int nch = (n + per - 1) / per;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    HostPipe pp;
+    if (cudaStreamCreateWithFlags(&pp.up, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pp.down, cudaStreamNonBlocking) != cudaSuccess)
+        return OF_ECUDA;
+    cudaEvent_t start = pp.make();
+    if (!start || cudaEventRecord(start, st) != cudaSuccess || cudaStreamWaitEvent(pp.up, start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(pp.down, start, 0) != cudaSuccess)
+        return OF_ECUDA;
+    const size_t in_elem = hs[0]->plan.in_format == OF_U8 ? 1 : 2;
+    std::vector<const void *> d1(per);
+    for (int c = 0; c < nch; ++c) {
+        const int off = c * per, cnt = off + per <= n ? per : n - off;
+        for (int i = off; i < off + cnt; ++i) {
+            const size_t px = (size_t)hs[i]->plan.H * hs[i]->plan.W;
+            if ((hI1s[i] && cudaMemcpyAsync(dI1s[i], hI1s[i], px * in_elem, cudaMemcpyHostToDevice, pp.up) != cudaSuccess) ||
+                cudaMemcpyAsync(dI2s[i], hI2s[i], px * in_elem, cudaMemcpyHostToDevice, pp.up) != cudaSuccess)
+                return OF_ECUDA;
+            d1[i - off] = hI1s[i] ? dI1s[i] : nullptr;
+        }
+        cudaEvent_t in = pp.make(), done = pp.make();
+        if (!in || !done || cudaEventRecord(in, pp.up) != cudaSuccess || cudaStreamWaitEvent(st, in, 0) != cudaSuccess)
+            return OF_ECUDA;
+        const Tuning t = tuning_for(hs[0]->plan, batch_size_class(cnt, hs + off));
+        const int rc = run_batch(cnt, hs + off, d1.data(), dI2s + off, dus + off, dvs + off, st, t);
+        if (rc != OF_OK) return rc;
+        if (cudaEventRecord(done, st) != cudaSuccess || cudaStreamWaitEvent(pp.down, done, 0) != cudaSuccess)
+            return OF_ECUDA;
+        for (int i = off; i < off + cnt; ++i) {
+            const size_t bytes = (size_t)hs[i]->plan.H * hs[i]->plan.W * sizeof(float);
+            if (cudaMemcpyAsync(hus[i], dus[i], bytes, cudaMemcpyDeviceToHost, pp.down) != cudaSuccess ||
+                cudaMemcpyAsync(hvs[i], dvs[i], bytes, cudaMemcpyDeviceToHost, pp.down) != cudaSuccess)
+                return OF_ECUDA;
+        }
+    }
+    cudaEvent_t end = pp.make();
+    if (!end || cudaEventRecord(end, pp.down) != cudaSuccess || cudaStreamWaitEvent(st, end, 0) != cudaSuccess)
+        return OF_ECUDA;
+    return OF_OK;
 }

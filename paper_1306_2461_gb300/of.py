@@ -88,6 +88,7 @@ def _load():
         "of_sbubble_count": (ctypes.c_int, [vp, i32, i32, ctypes.c_float, vp, vp]),
         "of_field_minmax": (ctypes.c_int, [vp, i32, i32, vp, vp]),
         "of_debug_fail_allocs": (ctypes.c_int, [i32]),
+        "of_compute_batch_host": (ctypes.c_int, [i32, pp, pp, pp, pp, pp, pp, pp, pp, pp, vp, i32]),
         "of_autotune_batch": (ctypes.c_int, [i32, pp, pp, pp, pp, pp, vp, i32, ctypes.POINTER(Tuning),
                                              ctypes.POINTER(Tuning), i32, ctypes.POINTER(i32)]),
         "of_batch_size_class": (ctypes.c_int, [i32, pp, ctypes.POINTER(i32)]),
@@ -251,6 +252,36 @@ def _batch_ptrs(flows, I1s, I2s, us, vs):
     au = _ptr_array([_flow_ptr(us[i], flows[i].plan, "u") for i in range(n)])
     av = _ptr_array([_flow_ptr(vs[i], flows[i].plan, "v") for i in range(n)])
     return hs, a1, a2, au, av
+
+
+def _host_ptr(t: torch.Tensor | None, dtype, p: Plan, name: str) -> int | None:
+    if t is None:
+        return None
+    if t.is_cuda or t.dtype != dtype or tuple(t.shape) != (p.H, p.W) or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous host {dtype} tensor of shape ({p.H}, {p.W}) "
+                         "(pinned for asynchronous copies)")
+    return t.data_ptr()
+
+
+def compute_batch_host(flows, hI1s, hI2s, hus, hvs, dI1s, dI2s, dus, dvs, stream=None, chunk=0):
+    """of_compute_batch_host: frames from host tensors, fields into host tensors, the
+    copies overlapped with the batched launches (chunks of `chunk` pairs, 0 = four
+    chunks). hI1s[i] = None reuses the previous pyramid. Synchronise `stream` before
+    reading hus/hvs."""
+    n = len(flows)
+    img = [torch.uint8 if f.plan.in_format == OF_U8 else torch.uint16 for f in flows]
+    arrs = [
+        _ptr_array([f.handle.value for f in flows]),
+        _ptr_array([_host_ptr(hI1s[i], img[i], flows[i].plan, "hI1") for i in range(n)]),
+        _ptr_array([_host_ptr(hI2s[i], img[i], flows[i].plan, "hI2") for i in range(n)]),
+        _ptr_array([_host_ptr(hus[i], torch.float32, flows[i].plan, "hu") for i in range(n)]),
+        _ptr_array([_host_ptr(hvs[i], torch.float32, flows[i].plan, "hv") for i in range(n)]),
+        _ptr_array([_img_ptr(dI1s[i], flows[i].plan, "dI1") if hI1s[i] is not None else None for i in range(n)]),
+        _ptr_array([_img_ptr(dI2s[i], flows[i].plan, "dI2") for i in range(n)]),
+        _ptr_array([_flow_ptr(dus[i], flows[i].plan, "du") for i in range(n)]),
+        _ptr_array([_flow_ptr(dvs[i], flows[i].plan, "dv") for i in range(n)]),
+    ]
+    _check(_lib.of_compute_batch_host(n, *arrs, _stream(stream), int(chunk)), "of_compute_batch_host")
 
 
 def autotune_batch(flows, I1s, I2s, us=None, vs=None, stream=None, reps=3):

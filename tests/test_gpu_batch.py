@@ -139,3 +139,56 @@ def test_batch_rejects_mixed_methods_and_repeats(of):
     with pytest.raises(of.OfError) as ei:
         of.compute_batch([a, c], [I, None], [I, I])
     assert ei.value.status == of.OF_ESTATE
+
+
+@pytest.mark.parametrize("chunk", [0, 1, 3, 64])
+def test_host_buffer_pipeline_equals_device_batch(of, chunk):
+    # frames from pinned host memory, fields back to pinned host memory, copies
+    # overlapped with the chunked launches: the same bits as of_compute_batch, including
+    # pairs that reuse their previous pyramid
+    import torch
+    from paper_1306_2461_gb300 import serve
+    streams = [synth.ParticleStream(*hw, seed=20 + k) for k, hw in
+               enumerate([(160, 224), (96, 128), (160, 224), (200, 136), (96, 128)])]
+    frames = []
+    for st in streams:
+        fr = []
+        for _ in range(3):
+            fr.append(st.frame())
+            st.advance()
+        frames.append(fr)
+    n = len(streams)
+    plans = [of.Plan.make(*fr[0].shape, 3, 4, 3, bits=12, storage="f16") for fr in frames]
+    fa = [of.Flow(p) for p in plans]
+    fb = [of.Flow(p) for p in plans]
+    hI = [[serve.pinned_frame(x) for x in fr] for fr in frames]
+    dI1 = [to_dev(fr[0]) for fr in frames]
+    dI2 = [to_dev(fr[1]) for fr in frames]
+    hu = [torch.empty(fr[0].shape, dtype=torch.float32).pin_memory() for fr in frames]
+    hv = [torch.empty(fr[0].shape, dtype=torch.float32).pin_memory() for fr in frames]
+    du = [torch.empty(fr[0].shape, dtype=torch.float32, device="cuda") for fr in frames]
+    dv = [torch.empty(fr[0].shape, dtype=torch.float32, device="cuda") for fr in frames]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        of.compute_batch_host(fa, [h[0] for h in hI], [h[1] for h in hI], hu, hv, dI1, dI2, du, dv,
+                              stream=s, chunk=chunk)
+        ub, vb = of.compute_batch(fb, [to_dev(fr[0]) for fr in frames], [to_dev(fr[1]) for fr in frames],
+                                  stream=s)
+    s.synchronize()
+    for i in range(n):
+        assert torch.equal(hu[i], ub[i].cpu()) and torch.equal(hv[i], vb[i].cpu()), i
+    # second step: odd pairs reuse their previous pyramid
+    reuse = [None if i % 2 else hI[i][1] for i in range(n)]
+    dI1b = [to_dev(frames[i][1]) for i in range(n)]
+    with torch.cuda.stream(s):
+        of.compute_batch_host(fa, reuse, [h[2] for h in hI], hu, hv, dI1b, dI2, du, dv, stream=s, chunk=chunk)
+        ub, vb = of.compute_batch(fb, [None if i % 2 else to_dev(frames[i][1]) for i in range(n)],
+                                  [to_dev(fr[2]) for fr in frames], stream=s)
+    s.synchronize()
+    for i in range(n):
+        assert torch.equal(hu[i], ub[i].cpu()) and torch.equal(hv[i], vb[i].cpu()), i
+    with pytest.raises(of.OfError):       # a handle twice
+        of.compute_batch_host([fa[0], fa[0]], [hI[0][0]] * 2, [hI[0][1]] * 2, hu[:1] * 2, hv[:1] * 2,
+                              dI1[:1] * 2, dI2[:1] * 2, du[:1] * 2, dv[:1] * 2, stream=s)
+    for f in fa + fb:
+        f.close()
