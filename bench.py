@@ -5,8 +5,9 @@
 the fraction of the HBM roofline.
 
 One step = the whole method (pyramids + all iterations on all levels) for a batch of
-pairs, one persistent launch through of_compute_batch; inputs are resident in HBM when
-the timed region starts and the step's working set is far above the L2 size.
+pairs through of_compute_batch: one CUDA graph replay of the phase launches (or of the
+persistent launch, if the autotuner picks it); inputs are resident in HBM when the
+timed region starts and the step's working set is far above the L2 size.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
 
@@ -76,9 +77,9 @@ def kernel_source_hash():
 
 
 def recorded_traffic(kernel_hash):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this
-    exact kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "batch_kernel_pair1024_traffic.txt")
+    """DRAM bytes per step (all kernels of one graph replay) from the committed ncu
+    summary, if it was taken on this exact kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "batch_step_pair1024_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -89,7 +90,7 @@ def recorded_traffic(kernel_hash):
     if kv.get("kernel_source_sha1") != kernel_hash:
         return None
     try:
-        return float(kv["bytes_per_launch_full_batch"])
+        return float(kv["bytes_per_step_full_batch"])
     except (KeyError, ValueError):
         return None
 
@@ -329,6 +330,11 @@ def main():
             dist.destroy_process_group()
         return 0
     alg, alg_pyr, alg_it = algorithmic_bytes(H, W, LEVELS, ITERS, 2, 2)
+    phased = tuning["best"]["phased"] if tuning else 1
+    groups = (B + 63) // 64
+    launches_per_step = groups * (max(LEVELS - 1, 1) + LEVELS * ITERS) if phased else 1
+    step_kernels = (f"batch step: {groups * max(LEVELS - 1, 1)} phase_pyr_kernel + {groups * LEVELS * ITERS} "
+                    "phase_iter_kernel launches" if phased else "batch step: 1 persistent batch_kernel launch")
     peak, peak_kind = measured_peaks()
     launch_ms = statistics.mean(step_ms)
     achieved = alg * B / (launch_ms / 1000.0) / 1e9
@@ -341,26 +347,27 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "f16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "H": H, "W": W, "bits": BITS, "levels": LEVELS, "radius": RADIUS,
                    "iterations": ITERS, "pairs_per_step": B, "distinct_pairs": DISTINCT,
-                   "form": "batched persistent launch (of_compute_batch), CUDA graph",
-                   "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm")}
+                   "form": "batched (of_compute_batch), one CUDA graph replay per step",
+                   "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased")}
                               if tuning else "default (autotuner off)"),
                    "l2": "no flush: per-step working set ~%.1f GB >> 129 MB L2" % (
                        B * (of.workspace_bytes(plan16) + 4 * H * W) / 1e9),
                    "parallelism": f"replicas x{world}"},
-        "autotune_candidates_ms": ([[c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], round(c["ms"], 3)]
+        "autotune_candidates_ms": ([[c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"], round(c["ms"], 3)]
                                     for c in tuning["candidates"]] if tuning else None),
         "latency_ms": {"step_p50": percentile(step_ms, 50), "step_p99": percentile(step_ms, 99),
                        "step_max": max(step_ms)},
         "mpix_iter_per_s": pixel_iterations(H, W, LEVELS, ITERS) * value / 1e6,
         "epe_vs_ground_truth_px": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max()),
                                    "margin_px": m},
-        "roofline": {"bound": "hbm", "kernel": "batch_kernel (persistent, whole method)",
+        "roofline": {"bound": "hbm", "kernel": step_kernels,
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
-                     "algorithmic_bytes_per_launch": alg * B,
+                     "timed_unit": "one step = one CUDA graph launch, CUDA events around each on the launching stream",
+                     "algorithmic_bytes_per_step": alg * B,
                      "algorithmic_bytes_per_field": {"total": alg, "pyramids": alg_pyr, "iterations": alg_it},
                      "kernel_source_sha1": khash},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step,
         "host_wall_s": t_host,
     }
     if clocks:

@@ -164,12 +164,17 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
 /*
  * Autotuning of the batched launch (of_compute_batch and the serving loop). Every
  * batch shape has the same results to within the stated tolerances whichever tuning
- * runs it; the default tuning (no table entry) gives the results of of_compute bit for
- * bit. A tuning:
+ * runs it; with grouped sums (generic_sums == 0) they are the results of of_compute bit
+ * for bit. Without a table entry a batch runs {generic_sums 0, stage_i2 0,
+ * blocks_per_sm 0, phased 1}. A tuning:
  *   generic_sums   1: per-output window sums of the run-time-radius kernel;
  *                  0: grouped sums of the kernel specialised for the radius
  *   stage_i2       1: stage I2 footprints in shared memory (specialised kernel only)
  *   blocks_per_sm  resident blocks per SM of the persistent launch; 0 = as many as fit
+ *   phased         1: one ordinary launch per phase (pyramid pass, iteration) over all
+ *                  pairs' tiles, the pairs' arguments passed as kernel parameters, in
+ *                  place of the one persistent launch with grid barriers (then
+ *                  blocks_per_sm must be 0)
  *   ms             measured milliseconds per batch (of_autotune_batch output only)
  * The process-wide table is keyed by the method (in_format, storage, radius, levels,
  * iterations, OF_FLAG_ZNSSD) and a size class, round(log2(mean level-0 pixels per pair)).
@@ -178,6 +183,7 @@ typedef struct of_tuning {
     int32_t generic_sums;
     int32_t stage_i2;
     int32_t blocks_per_sm;
+    int32_t phased;
     float ms;
 } of_tuning;
 

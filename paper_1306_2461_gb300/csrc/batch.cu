@@ -41,6 +41,11 @@ struct BatchEntry {
     size_t smem = 0;
     int device = -1;
     uint64_t last_use = 0;
+    // phase launches: what to launch again when no graph could be captured
+    int phased = 0;
+    std::vector<BatchPair> pairs;
+    of_plan plan;
+    Tuning tuning;
 };
 
 constexpr int BATCH_CACHE = 8;
@@ -229,6 +234,117 @@ static Resolved resolve(const of_plan &p0, const Tuning &t)
     return r;
 }
 
+// The method for all pairs of a batch as ordinary launches, one per phase and group of
+// up to PHASE_PAIRS pairs (the per-pair arguments are kernel parameters): pyramid passes
+// (after the normalisation of Eq. 2 when the plan asks for it), then the iterations
+// level by level. Stream order separates the phases; there is no grid-wide barrier.
+static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_plan &p0, const Tuning &t,
+                                  cudaStream_t st)
+{
+    const int n = (int)pairs.size();
+    const int L = p0.levels;
+    const bool zn = (p0.flags & OF_FLAG_ZNSSD) != 0;
+    const int32_t stage = (!t.generic_sums && ((p0.flags & OF_FLAG_STAGE_I2) || t.stage_i2)) ? 1 : 0;
+    cudaError_t e;
+    for (int g0 = 0; g0 < n; g0 += PHASE_PAIRS) {
+        const int m = n - g0 < PHASE_PAIRS ? n - g0 : PHASE_PAIRS;
+        const BatchPair *bp = pairs.data() + g0;
+        if (zn) {
+            ZnPhase Z;
+            memset(&Z, 0, sizeof(Z));
+            Z.npairs = m;
+            for (int i = 0; i < m; ++i) {
+                ZnArgs &z = Z.a[i];
+                z.H = bp[i].H[0];
+                z.W = bp[i].W[0];
+                z.src_pitch = bp[i].W[0];
+                z.dst_pitch = bp[i].pitch[0];
+                z.tiles_x = (z.W + ZN_T - 1) / ZN_T;
+                z.tiles = z.tiles_x * ((z.H + ZN_T - 1) / ZN_T);
+                z.first_image = bp[i].first_image;
+                for (int k = 0; k < 2; ++k) {
+                    z.src[k] = bp[i].raw[k];
+                    z.dst[k] = bp[i].pyr[k] + bp[i].off[0];
+                }
+                Z.prefix[i + 1] = Z.prefix[i] + z.tiles * (2 - z.first_image);
+            }
+            if ((e = launch_phase_zn(Z, p0.in_format, p0.storage, st)) != cudaSuccess) return e;
+        }
+        // pyramid passes: level ls -> ls + 1; without the normalisation the first pass
+        // reads the camera images and stores level 0 as well
+        for (int ls = 0; ls < (L > 1 ? L - 1 : (zn ? 0 : 1)); ++ls) {
+            const bool first = !zn && ls == 0;
+            PyrPhase Q;
+            memset(&Q, 0, sizeof(Q));
+            Q.npairs = m;
+            for (int i = 0; i < m; ++i) {
+                PyrArgs &a = Q.a[i];
+                const int ld = ls + 1;
+                a.H = bp[i].H[ls];
+                a.W = bp[i].W[ls];
+                a.Ho = (a.H + 1) / 2;
+                a.Wo = (a.W + 1) / 2;
+                a.dst_pitch = ld < L ? bp[i].pitch[ld] : 0;
+                a.tiles_x = (a.Wo + PYR_TW - 1) / PYR_TW;
+                a.tiles = a.tiles_x * ((a.Ho + PYR_TH - 1) / PYR_TH);
+                a.first_image = bp[i].first_image;
+                for (int k = 0; k < 2; ++k) {
+                    a.dst[k] = ld < L ? bp[i].pyr[k] + bp[i].off[ld] : nullptr;
+                    a.dst0[k] = first ? bp[i].pyr[k] + bp[i].off[0] : nullptr;
+                    a.src[k] = first ? bp[i].raw[k] : bp[i].pyr[k] + bp[i].off[ls];
+                }
+                a.src_pitch = first ? bp[i].W[0] : bp[i].pitch[ls];
+                a.dst0_pitch = first ? bp[i].pitch[0] : 0;
+                Q.prefix[i + 1] = Q.prefix[i] + a.tiles * (2 - a.first_image);
+            }
+            if ((e = launch_phase_pyr(Q, first, p0.in_format, p0.storage, st)) != cudaSuccess) return e;
+        }
+        // iterations, coarsest level first; flow buffers ping-pong
+        for (int k = 0; k < L * p0.iterations; ++k) {
+            const int l = L - 1 - k / p0.iterations, it = k % p0.iterations, cur = k & 1;
+            IterPhase I;
+            memset(&I, 0, sizeof(I));
+            I.npairs = m;
+            for (int i = 0; i < m; ++i) {
+                IterArgs &a = I.a[i];
+                a.I1 = bp[i].pyr[0] + bp[i].off[l];
+                a.I2 = bp[i].pyr[1] + bp[i].off[l];
+                a.H = bp[i].H[l];
+                a.W = bp[i].W[l];
+                a.pitch = bp[i].pitch[l];
+                a.fin = bp[i].flow[cur];
+                a.fin_pitch = bp[i].pitch[l];
+                if (it == 0 && l == L - 1) {
+                    a.mode = FLOW_ZERO;
+                } else if (it == 0) {
+                    a.mode = FLOW_UPSAMPLE;
+                    a.fin_pitch = bp[i].pitch[l + 1];
+                    a.Hc = bp[i].H[l + 1];
+                    a.Wc = bp[i].W[l + 1];
+                } else {
+                    a.mode = FLOW_SAME;
+                }
+                if (l == 0 && it == p0.iterations - 1) {
+                    a.u_out = bp[i].u;
+                    a.v_out = bp[i].v;
+                } else {
+                    a.fout = bp[i].flow[1 - cur];
+                    a.fout_pitch = bp[i].pitch[l];
+                }
+                a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
+                a.tiles = a.tiles_x * ((a.H + LK_TH - 1) / LK_TH);
+                a.status = bp[i].status;
+                a.stage_i2 = stage;
+                I.prefix[i + 1] = I.prefix[i] + a.tiles;
+            }
+            if ((e = launch_phase_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, st)) !=
+                cudaSuccess)
+                return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 static int commit_state(int32_t n, const of_handle *hs, const BatchBuild &b, cudaStream_t st)
 {
     for (int i = 0; i < n; ++i) {
@@ -290,6 +406,11 @@ int batch_run_slot(BatchSlot &slot, int32_t n, const of_handle *hs, const void *
     memcpy(slot.host, b.pairs.data(), pairs_bytes);
     memcpy(slot.host + pairs_bytes, b.prefix.data(), prefix_bytes);
     const Tuning t = tuning_for(p0, batch_size_class(n, hs));
+    if (t.phased) {
+        if (enqueue_phased(b.pairs, p0, t, st) != cudaSuccess || cudaEventRecord(slot.done, st) != cudaSuccess)
+            return OF_ECUDA;
+        return commit_state(n, hs, b, st);
+    }
     const Resolved rv = resolve(p0, t);
     BatchHdr hd;
     fill_header(hd, p0, b, slot.dev, bar_off, rv.stage);
@@ -337,7 +458,7 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
         memcpy(k + pairs_bytes, b.prefix.data(), prefix_bytes);
         memcpy(k + pairs_bytes + prefix_bytes, &st, sizeof(st));
         const int extra[6] = {p0.radius, (int)(p0.iterations * 8 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD))),
-                              hs[0]->device, t.generic_sums, t.stage_i2, t.blocks_per_sm};
+                              hs[0]->device, t.generic_sums, t.stage_i2, t.blocks_per_sm + 256 * t.phased};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
 
@@ -373,18 +494,23 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
         fill_header(ne.hdr, p0, b, ne.dev, bar_off, rv.stage);
         ne.fn = rv.fn;
         ne.smem = rv.smem;
+        ne.phased = t.phased;
+        ne.plan = p0;
+        ne.tuning = t;
+        if (t.phased) ne.pairs = b.pairs;
         if ((rc = grid_for(ne.fn, ne.smem, ne.device, b.max_items, t.blocks_per_sm, ne.grid))) {
             release(ne);
             return rc;
         }
-        // capture [reset barrier, persistent kernel] as a graph when the stream allows it
+        // capture [reset barrier, persistent kernel] or the phase launches as a graph when
+        // the stream allows it
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         const bool graphs = st != nullptr && !(p0.flags & OF_FLAG_NO_GRAPH) &&
                             cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
         if (graphs) {
             cudaGraph_t g = nullptr;
             if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                const cudaError_t le = launch_direct(ne, st);
+                const cudaError_t le = ne.phased ? enqueue_phased(ne.pairs, ne.plan, ne.tuning, st) : launch_direct(ne, st);
                 const cudaError_t ce = cudaStreamEndCapture(st, &g);
                 if (le == cudaSuccess && ce == cudaSuccess && g &&
                     cudaGraphInstantiate(&ne.exec, g, 0) != cudaSuccess)
@@ -396,7 +522,8 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
         e = &ne;
     }
     e->last_use = g_clock;
-    cudaError_t err = e->exec ? cudaGraphLaunch(e->exec, st) : launch_direct(*e, st);
+    cudaError_t err = e->exec ? cudaGraphLaunch(e->exec, st)
+                              : (e->phased ? enqueue_phased(e->pairs, e->plan, e->tuning, st) : launch_direct(*e, st));
     if (err != cudaSuccess) return OF_ECUDA;
     if (cudaEventRecord(e->done, st) != cudaSuccess) return OF_ECUDA;
     return commit_state(n, hs, b, st);

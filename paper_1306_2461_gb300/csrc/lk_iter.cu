@@ -45,6 +45,17 @@ cudaError_t launch_i1_iter(const IterArgs &a, int elem, int radius, float fp64_c
     }
 }
 
+#define OF_CASE_PH(R) \
+    case R: return phase_launch<R>(P, elem, radius, fp64_cond, s);
+cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond, cudaStream_t s)
+{
+    if (generic) return phase_launch<0>(P, elem, radius, fp64_cond, s);
+    switch (radius) {
+        OF_RADII(OF_CASE_PH)
+    default: return phase_launch<0>(P, elem, radius, fp64_cond, s);
+    }
+}
+
 #define OF_CASE_BK(R) \
     case R: return batch_kernel_ptr<R>(in_format, storage);
 void *batch_kernel_for(int in_format, int storage, int radius)

@@ -74,7 +74,8 @@ cudaError_t dev_malloc(void **p, size_t bytes);
 struct Tuning {
     int generic_sums = 0;    // 1: the run-time-radius kernel (per-output sums); 0: grouped fixed-radius sums
     int stage_i2 = 0;        // 1: stage I2 footprints in shared memory (fixed-radius kernel only)
-    int blocks_per_sm = 0;   // resident blocks per SM; 0 = as many as fit
+    int blocks_per_sm = 0;   // resident blocks per SM of the persistent launch; 0 = as many as fit
+    int phased = 1;          // 1: one ordinary launch per phase; 0: the persistent launch with grid barriers
 };
 // The tuning table entry for this method and size class, or the default.
 Tuning tuning_for(const of_plan &method, int size_class);

@@ -118,6 +118,20 @@ constexpr int ZN_RADIUS = 5;          // Sect. 2.4: a radius of 5 pixels
 constexpr int ZN_T = 32;              // output tile
 constexpr int ZN_EPS = 1;             // added to the local variance (counts squared)
 
+// One launch of a phase of the batched method over up to PHASE_PAIRS pairs: the pairs'
+// arguments travel as a kernel parameter (constant space, warp-uniform), and block b
+// works on tile b - prefix[p] of the pair p with prefix[p] <= b < prefix[p + 1].
+constexpr int PHASE_PAIRS = 64;
+template <typename A> struct Phase {
+    int32_t npairs;
+    int32_t prefix[PHASE_PAIRS + 1];
+    A a[PHASE_PAIRS];
+};
+using IterPhase = Phase<IterArgs>;
+using PyrPhase = Phase<PyrArgs>;
+using ZnPhase = Phase<ZnArgs>;
+static_assert(sizeof(IterPhase) <= 32000 && sizeof(PyrPhase) <= 32000, "kernel parameters are limited to 32 KB");
+
 // Tile shapes.
 constexpr int LK_TW = 64;    // iteration output tile width
 #ifndef OF_LK_TH
@@ -151,6 +165,10 @@ cudaError_t launch_window_sums(const float *ch, int H, int W, int r, float *out,
 // then iterations that read it from a.hess.
 cudaError_t launch_i1_hess(const HessArgs &a, int elem, int radius, cudaStream_t s);
 cudaError_t launch_i1_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s);
+// Phase launches of the batched method (grid = P.prefix[P.npairs] blocks).
+cudaError_t launch_phase_pyr(const PyrPhase &P, bool first, int in_format, int storage, cudaStream_t s);
+cudaError_t launch_phase_zn(const ZnPhase &P, int in_format, int storage, cudaStream_t s);
+cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond, cudaStream_t s);
 void *batch_kernel_for(int in_format, int storage, int radius);
 size_t batch_smem_bytes(int radius, bool stage_i2);
 void *batch_kernel_generic(int in_format, int storage);   // the run-time-radius kernel
@@ -163,6 +181,7 @@ cudaError_t configure_lk_kernels();   // all kernels with dynamic shared memory,
 template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
 template <int R> cudaError_t i1h_launch(const HessArgs &a, int elem, int r, cudaStream_t s);
+template <int R> cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> cudaError_t i1_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> void *batch_kernel_ptr(int in_format, int storage);
 template <int R> cudaError_t radius_configure();

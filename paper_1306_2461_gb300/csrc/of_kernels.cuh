@@ -39,6 +39,18 @@ constexpr int PYR_RH = 2 * PYR_TH + 3;
 constexpr int PYR_RW = 2 * PYR_TW + 3;
 constexpr int PYR_SMEM_FLOATS = PYR_RH * PYR_RW + PYR_RH * PYR_TW;
 
+// The pair of block b in a phase launch: the largest p with prefix[p] <= b.
+__device__ __forceinline__ int phase_pair(const int32_t *prefix, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // [1 4 6 4 1] . (a, b, c, d, e), with its roundings fixed: (a + e) + 4 (b + d) + 6 c.
 __device__ __forceinline__ float binom5(float a, float b, float c, float d, float e)
 {

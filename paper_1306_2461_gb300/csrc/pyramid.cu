@@ -74,6 +74,75 @@ cudaError_t launch_znssd(const ZnArgs &a, int in_format, int storage, cudaStream
     }
 }
 
+// ------------------------------------------------------------ phase launches
+// One pyramid pass of up to PHASE_PAIRS pairs (both images, or only the second when the
+// first is reused); the pairs' arguments are a kernel parameter.
+template <typename Tin, typename Tout, bool FIRST>
+__global__ void __launch_bounds__(PYR_THREADS) phase_pyr_kernel(const __grid_constant__ PyrPhase P)
+{
+    const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
+    const PyrArgs &a = P.a[p];
+    const int j = blockIdx.x - P.prefix[p];
+    const int img = a.first_image + j / a.tiles;
+    pyr_tile<Tin, Tout, FIRST>(a, j - (j / a.tiles) * a.tiles, img);
+}
+
+template <typename Tout>
+static cudaError_t phase_first_for(const PyrPhase &P, int in_format, cudaStream_t s)
+{
+    if (in_format == OF_U8)
+        phase_pyr_kernel<uint8_t, Tout, true><<<P.prefix[P.npairs], PYR_THREADS, 0, s>>>(P);
+    else
+        phase_pyr_kernel<uint16_t, Tout, true><<<P.prefix[P.npairs], PYR_THREADS, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_pyr(const PyrPhase &P, bool first, int in_format, int storage, cudaStream_t s)
+{
+    const int blocks = P.prefix[P.npairs];
+    if (blocks == 0) return cudaSuccess;
+    if (first) {
+        switch (storage) {
+        case OF_F32: return phase_first_for<float>(P, in_format, s);
+        case OF_F16: return phase_first_for<__half>(P, in_format, s);
+        default: return phase_first_for<__nv_bfloat16>(P, in_format, s);
+        }
+    }
+    switch (storage) {
+    case OF_F32: phase_pyr_kernel<float, float, false><<<blocks, PYR_THREADS, 0, s>>>(P); break;
+    case OF_F16: phase_pyr_kernel<__half, __half, false><<<blocks, PYR_THREADS, 0, s>>>(P); break;
+    default: phase_pyr_kernel<__nv_bfloat16, __nv_bfloat16, false><<<blocks, PYR_THREADS, 0, s>>>(P); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) phase_zn_kernel(const __grid_constant__ ZnPhase P)
+{
+    __shared__ float smem[ZN_SMEM_FLOATS];
+    const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
+    const ZnArgs &a = P.a[p];
+    const int j = blockIdx.x - P.prefix[p];
+    znssd_tile<Tin, Tout, true>(a, j - (j / a.tiles) * a.tiles, a.first_image + j / a.tiles, smem);
+}
+
+template <typename Tout> static cudaError_t phase_zn_for(const ZnPhase &P, int in_format, cudaStream_t s)
+{
+    if (in_format == OF_U8) phase_zn_kernel<uint8_t, Tout><<<P.prefix[P.npairs], 256, 0, s>>>(P);
+    else phase_zn_kernel<uint16_t, Tout><<<P.prefix[P.npairs], 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_zn(const ZnPhase &P, int in_format, int storage, cudaStream_t s)
+{
+    if (P.prefix[P.npairs] == 0) return cudaSuccess;
+    switch (storage) {
+    case OF_F32: return phase_zn_for<float>(P, in_format, s);
+    case OF_F16: return phase_zn_for<__half>(P, in_format, s);
+    default: return phase_zn_for<__nv_bfloat16>(P, in_format, s);
+    }
+}
+
 template <typename T>
 __global__ void level_to_f32_kernel(Level l, float *dst)
 {

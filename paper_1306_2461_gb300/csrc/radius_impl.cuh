@@ -23,6 +23,20 @@ __global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>()) lk_iter_kernel
     lk_tile<T, true, R>(a, blockIdx.x, r, fp64_cond, smem, phase);
 }
 
+// One iteration of up to PHASE_PAIRS pairs on one level: block b runs tile
+// b - prefix[p] of pair p. The same tile code as lk_iter_kernel, so the same results.
+template <typename T, int R>
+__global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>())
+phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
+{
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
+    uint32_t phase = 0;
+    lk_tile_prepare<R>(smem);
+    lk_tile<T, true, R>(P.a[p], blockIdx.x - P.prefix[p], r, fp64_cond, smem, phase);
+}
+
 // The window sums of five given planes, through the same passes as the iteration tile.
 template <int R>
 __global__ void __launch_bounds__(LK_THREADS)
@@ -115,6 +129,27 @@ template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, flo
     return cudaGetLastError();
 }
 
+template <typename T, int R>
+static cudaError_t phase_for(const IterPhase &P, int r, float fp64_cond, cudaStream_t s)
+{
+    const bool stage = P.npairs > 0 && P.a[0].stage_i2 != 0;
+    phase_iter_kernel<T, R><<<P.prefix[P.npairs], LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r, stage), s>>>(
+        P, r, fp64_cond);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, cudaStream_t s)
+{
+    if (P.prefix[P.npairs] == 0) return cudaSuccess;
+    switch (elem) {
+    case ET_U8: return phase_for<uint8_t, R>(P, r, fp64_cond, s);
+    case ET_U16: return phase_for<uint16_t, R>(P, r, fp64_cond, s);
+    case ET_F32: return phase_for<float, R>(P, r, fp64_cond, s);
+    case ET_F16: return phase_for<__half, R>(P, r, fp64_cond, s);
+    default: return phase_for<__nv_bfloat16, R>(P, r, fp64_cond, s);
+    }
+}
+
 template <typename T, int R> static cudaError_t i1h_for(const HessArgs &a, int r, cudaStream_t s)
 {
     i1_hess_kernel<T, R><<<a.tiles, LK_THREADS, sizeof(float) * i1_smem_floats<R>(r, 3), s>>>(a, r);
@@ -172,6 +207,11 @@ template <int R> cudaError_t radius_configure()
     OF_SET((lk_iter_kernel<float, R>));
     OF_SET((lk_iter_kernel<__half, R>));
     OF_SET((lk_iter_kernel<__nv_bfloat16, R>));
+    OF_SET((phase_iter_kernel<uint8_t, R>));
+    OF_SET((phase_iter_kernel<uint16_t, R>));
+    OF_SET((phase_iter_kernel<float, R>));
+    OF_SET((phase_iter_kernel<__half, R>));
+    OF_SET((phase_iter_kernel<__nv_bfloat16, R>));
     OF_SET((window_sums_kernel<R>));
     {
         const int r = R == 0 ? MAX_RADIUS : R;
@@ -198,6 +238,7 @@ template <int R> cudaError_t radius_configure()
 template cudaError_t lk_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template cudaError_t ws_launch<OF_RADIUS>(const float *, int, int, int, float *, cudaStream_t);
 template cudaError_t i1h_launch<OF_RADIUS>(const HessArgs &, int, int, cudaStream_t);
+template cudaError_t phase_launch<OF_RADIUS>(const IterPhase &, int, int, float, cudaStream_t);
 template cudaError_t i1_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template void *batch_kernel_ptr<OF_RADIUS>(int, int);
 template cudaError_t radius_configure<OF_RADIUS>();

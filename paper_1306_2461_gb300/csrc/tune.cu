@@ -1,8 +1,9 @@
-// The autotuner of the persistent batched launch. A process-wide table maps a method
-// (input format, storage, radius, levels, iterations, normalisation) and a size class
+// The autotuner of the batched launch. A process-wide table maps a method (input
+// format, storage, radius, levels, iterations, normalisation) and a size class
 // (round(log2(mean level-0 pixels per pair))) to a Tuning: window-sum strategy, I2
-// staging and resident blocks per SM. of_compute_batch and the serving loop read it;
-// of_autotune_batch fills it by timing every candidate on the caller's own batch.
+// staging, and either phase launches or the persistent launch at some resident blocks
+// per SM. of_compute_batch and the serving loop read it; of_autotune_batch fills it by
+// timing every candidate on the caller's own batch.
 #include <math.h>
 #include <string.h>
 
@@ -36,8 +37,21 @@ bool radius_is_specialised(int r)
     return false;
 }
 
-bool valid(const Tuning &t) { return t.generic_sums >= 0 && t.generic_sums <= 1 && t.stage_i2 >= 0 && t.stage_i2 <= 1 &&
-                                     t.blocks_per_sm >= 0 && t.blocks_per_sm <= 64 && !(t.generic_sums && t.stage_i2); }
+bool valid(const Tuning &t)
+{
+    return t.generic_sums >= 0 && t.generic_sums <= 1 && t.stage_i2 >= 0 && t.stage_i2 <= 1 && t.blocks_per_sm >= 0 &&
+           t.blocks_per_sm <= 64 && t.phased >= 0 && t.phased <= 1 && !(t.generic_sums && t.stage_i2) &&
+           !(t.phased && t.blocks_per_sm);
+}
+
+void to_c(const Tuning &t, float ms, of_tuning *o)
+{
+    o->generic_sums = t.generic_sums;
+    o->stage_i2 = t.stage_i2;
+    o->blocks_per_sm = t.blocks_per_sm;
+    o->phased = t.phased;
+    o->ms = ms;
+}
 
 }  // namespace
 
@@ -81,10 +95,7 @@ int of_tuning_get(const of_plan *method, int32_t size_class, of_tuning *t)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_table.find(key_of(*method, size_class));
     if (it == g_table.end()) return OF_ESTATE;
-    t->generic_sums = it->second.generic_sums;
-    t->stage_i2 = it->second.stage_i2;
-    t->blocks_per_sm = it->second.blocks_per_sm;
-    t->ms = 0.0f;
+    to_c(it->second, 0.0f, t);
     return OF_OK;
 }
 
@@ -95,6 +106,7 @@ int of_tuning_set(const of_plan *method, int32_t size_class, const of_tuning *t)
     v.generic_sums = t->generic_sums;
     v.stage_i2 = t->stage_i2;
     v.blocks_per_sm = t->blocks_per_sm;
+    v.phased = t->phased;
     if (!valid(v)) return OF_EINVAL;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_table[key_of(*method, size_class)] = v;
@@ -119,17 +131,19 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const of_plan &p0 = hs[0]->plan;
     // candidates: the grouped fixed-radius sums (gathered or staged I2) when the radius
-    // has a specialised kernel, the per-output sums of the run-time-radius kernel, each
-    // at full occupancy and at 1 and 2 blocks per SM
+    // has a specialised kernel, the per-output sums of the run-time-radius kernel; each
+    // as phase launches, and as the persistent launch at full occupancy and at 2 and 1
+    // blocks per SM
     std::vector<Tuning> cand;
-    const int occ[3] = {0, 2, 1};
+    const int occ[4] = {-1, 0, 2, 1};   // -1: phase launches
     for (int gs = radius_is_specialised(p0.radius) ? 0 : 1; gs <= 1; ++gs)
         for (int sg = 0; sg <= (gs ? 0 : 1); ++sg)
             for (int b : occ) {
                 Tuning t;
                 t.generic_sums = gs;
                 t.stage_i2 = sg;
-                t.blocks_per_sm = b;
+                t.phased = b < 0 ? 1 : 0;
+                t.blocks_per_sm = b < 0 ? 0 : b;
                 cand.push_back(t);
             }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -157,13 +171,7 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
             if (s != OF_OK) rc = s;
         }
         if (rc != OF_OK) break;
-        if (nres < max_results) {
-            results[nres].generic_sums = cand[c].generic_sums;
-            results[nres].stage_i2 = cand[c].stage_i2;
-            results[nres].blocks_per_sm = cand[c].blocks_per_sm;
-            results[nres].ms = ms;
-            ++nres;
-        }
+        if (nres < max_results) to_c(cand[c], ms, &results[nres++]);
         if (ibest < 0 || ms < best_ms) {
             ibest = (int)c;
             best_ms = ms;
@@ -177,12 +185,7 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_table[key_of(p0, batch_size_class(n, hs))] = cand[ibest];
     }
-    if (best) {
-        best->generic_sums = cand[ibest].generic_sums;
-        best->stage_i2 = cand[ibest].stage_i2;
-        best->blocks_per_sm = cand[ibest].blocks_per_sm;
-        best->ms = best_ms;
-    }
+    if (best) to_c(cand[ibest], best_ms, best);
     return OF_OK;
 }
 

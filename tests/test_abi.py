@@ -103,5 +103,9 @@ def test_tuning_table_host_calls(of):
         of.tuning_set(m, 20, generic_sums=1, stage_i2=1)                  # staging needs the grouped kernel
     with pytest.raises(of.OfError):
         of.tuning_set(m, 20, blocks_per_sm=-1)
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, blocks_per_sm=2, phased=1)                   # occupancy is a persistent-launch knob
+    of.tuning_set(m, 20, phased=1)
+    assert of.tuning_get(m, 20)["phased"] == 1
     of.tuning_clear()
     assert of.tuning_get(m, 20) is None

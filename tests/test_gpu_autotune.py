@@ -43,13 +43,13 @@ def test_every_candidate_matches_the_per_pair_path(of, oracle_mod):
     torch.cuda.synchronize()
     best, cands = of.autotune_batch(flows, I1, I2, reps=2)
     print(best, cands)
-    assert len(cands) == 9 and best["ms"] == min(c["ms"] for c in cands)
+    assert len(cands) == 12 and best["ms"] == min(c["ms"] for c in cands)
     sc = of.batch_size_class(flows)
     t = of.tuning_get(flows[0].plan, sc)
-    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"]) == \
-        (best["generic_sums"], best["stage_i2"], best["blocks_per_sm"])
+    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"], t["phased"]) == \
+        (best["generic_sums"], best["stage_i2"], best["blocks_per_sm"], best["phased"])
     for c in cands:
-        of.tuning_set(flows[0].plan, sc, c["generic_sums"], c["stage_i2"], c["blocks_per_sm"])
+        of.tuning_set(flows[0].plan, sc, c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"])
         us, vs = of.compute_batch(flows, I1, I2)
         torch.cuda.synchronize()
         for k in range(len(sizes)):
@@ -75,13 +75,13 @@ def test_cache_file_round_trip(of, tmp_path):
     path = str(tmp_path / "tune.json")
     ent = autotune.tune(flows, I1, I2, reps=1, path=path)
     sc = of.batch_size_class(flows)
-    assert ent["size_class"] == sc and len(ent["candidates"]) == 9
+    assert ent["size_class"] == sc and len(ent["candidates"]) == 12
     of.tuning_clear()
     assert of.tuning_get(flows[0].plan, sc) is None
     assert autotune.load(path) == 1
     t = of.tuning_get(flows[0].plan, sc)
-    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"]) == \
-        (ent["best"]["generic_sums"], ent["best"]["stage_i2"], ent["best"]["blocks_per_sm"])
+    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"], t["phased"]) == \
+        (ent["best"]["generic_sums"], ent["best"]["stage_i2"], ent["best"]["blocks_per_sm"], ent["best"]["phased"])
     again = autotune.ensure(flows, I1, I2, path=path)      # known: no new timing
     assert again["candidates"] == [] and again["best"]["generic_sums"] == ent["best"]["generic_sums"]
     of.tuning_clear()
@@ -95,3 +95,53 @@ def test_autotune_refuses_reused_pyramids(of):
         of.autotune_batch(flows, [None], I2, reps=1)
     assert ei.value.status == of.OF_EINVAL
     flows[0].close()
+
+
+def test_phase_launches_in_batches_with_reuse_and_in_the_server(of):
+    # the phase-launch mode forced through the table for every size class: batched pairs
+    # that reuse their previous pyramid, and the serving loop, give of_compute's bits
+    import torch
+    from paper_1306_2461_gb300 import serve
+    m = of.Plan.make(64, 64, 3, 4, 3, bits=12, storage="f16")
+    for sc in range(8, 27):
+        of.tuning_set(m, sc, phased=1)
+    sizes = [(160, 224), (96, 128), (192, 160)]
+    frames = []
+    for k, (H, W) in enumerate(sizes):
+        st = synth.ParticleStream(H, W, seed=40 + k)
+        fr = []
+        for _ in range(3):
+            fr.append(st.frame())
+            st.advance()
+        frames.append(fr)
+    plans = [of.Plan.make(H, W, 3, 4, 3, bits=12, storage="f16") for H, W in sizes]
+    flows = [of.Flow(p) for p in plans]
+    of.compute_batch(flows, [to_dev(f[0]) for f in frames], [to_dev(f[1]) for f in frames])
+    ub, vb = of.compute_batch(flows, [None, to_dev(frames[1][1]), None], [to_dev(f[2]) for f in frames])
+    torch.cuda.synchronize()
+    for k, p in enumerate(plans):
+        with of.Flow(p) as f:
+            u1, v1 = f.compute(to_dev(frames[k][1]), to_dev(frames[k][2]))
+            torch.cuda.synchronize()
+        assert torch.equal(ub[k], u1) and torch.equal(vb[k], v1), k
+    with serve.Server(levels=3, radius=4, iterations=3, bits=12, storage="f16", max_batch=8) as srv:
+        sids = [srv.open_stream(H, W) for H, W in sizes]
+        outs = {}
+        for j in range(3):
+            for k, sid in enumerate(sids):
+                u = torch.empty(sizes[k], device="cuda")
+                v = torch.empty(sizes[k], device="cuda")
+                outs[(k, j)] = (u, v)
+                srv.submit(sid, serve.pinned_frame(frames[k][j]), u, v, tag=10 * k + j)
+        srv.drain()
+        res = srv.poll(0)
+        assert all(r["status"] == 0 for r in res)
+    for k, p in enumerate(plans):
+        for j in (1, 2):
+            with of.Flow(p) as f:
+                u1, v1 = f.compute(to_dev(frames[k][j - 1]), to_dev(frames[k][j]))
+                torch.cuda.synchronize()
+            assert torch.equal(outs[(k, j)][0], u1) and torch.equal(outs[(k, j)][1], v1), (k, j)
+    of.tuning_clear()
+    for f in flows:
+        f.close()
