@@ -414,6 +414,28 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
                     (vs[0].cpu().double().numpy() - src[0].v_gt) ** 2)[m:-m, m:-m]
         out[key] = {"fields_per_s": K / (tot / 1000.0), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
                     "epe_vs_ground_truth_px": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}}
+    # the first-image-gradient variant in the batched form (phase launches), same workload
+    plan_v = of.Plan.make(H, W, LEVELS, RADIUS, ITERS, bits=BITS, storage="f16", flags=of.OF_FLAG_I1GRAD)
+    fv = [of.Flow(plan_v) for _ in range(len(flows))]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            of.compute_batch(fv, I1, I2, us, vs, stream=stream)
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        Kv = max(5, args.steps // 2)
+        a.record(stream)
+        for _ in range(Kv):
+            of.compute_batch(fv, I1, I2, us, vs, stream=stream)
+        b.record(stream)
+        stream.synchronize()
+    m = (RADIUS + 2) * 2 ** (LEVELS - 1)
+    e = np.sqrt((us[0].cpu().double().numpy() - src[0].u_gt) ** 2 +
+                (vs[0].cpu().double().numpy() - src[0].v_gt) ** 2)[m:-m, m:-m]
+    out["batched_f16_i1grad"] = {"fields_per_s": len(fv) * Kv / (a.elapsed_time(b) / 1000.0),
+                                 "ms_per_step": a.elapsed_time(b) / Kv,
+                                 "epe_vs_ground_truth_px": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}}
+    for f in fv:
+        f.close()
     # e2e: host (pinned) frames in, device compute, host flow fields out, every step
     B = len(flows)
     h1 = [torch.from_numpy(src[i % len(src)].I1.astype(np.int32)).to(torch.uint16).pin_memory() for i in range(B)]

@@ -67,9 +67,10 @@ typedef enum of_storage { OF_F32 = 0, OF_F16 = 1, OF_BF16 = 2 } of_storage;
                                  of the FIRST image at integer pixels (central difference, clamped)
                                  instead of the second image's gradient at the displaced position.
                                  The window matrix then depends on I1 only and is summed once per
-                                 level; each iteration sums two channels. Per-pair calls only:
-                                 of_compute_batch and of_server_create return OF_EINVAL for it.
-                                 The workspace grows by one float4 per level-0 pixel. */
+                                 level; each iteration sums two channels. Batched calls and the
+                                 serving loop run it as phase launches (the tuning's phased,
+                                 stage_i2 and blocks_per_sm are ignored for it). The workspace
+                                 grows by one float4 per level-0 pixel. */
 
 /*
  * Problem statement (Sect. 2.4): image size of the region of interest, number of

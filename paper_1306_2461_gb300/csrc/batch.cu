@@ -93,7 +93,8 @@ static bool same_method(const of_plan &a, const of_plan &b)
     return a.levels == b.levels && a.radius == b.radius && a.iterations == b.iterations &&
            a.in_format == b.in_format && a.in_bits == b.in_bits && a.storage == b.storage &&
            a.fp64_cond == b.fp64_cond &&
-           (a.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD)) == (b.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD));
+           (a.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD)) ==
+               (b.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD));
 }
 
 // The host image of one batch: descriptors, work-list prefix sums, slots, launch shape.
@@ -110,7 +111,7 @@ static int build_batch(int32_t n, const of_handle *hs, const void *const *I1s, c
     if (n < 0 || n > 65536 || !hs || !I1s || !I2s || !us || !vs) return OF_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!hs[i] || !I2s[i] || !us[i] || !vs[i]) return OF_EINVAL;
-        if (!same_method(hs[i]->plan, hs[0]->plan) || (hs[i]->plan.flags & OF_FLAG_I1GRAD)) return OF_EINVAL;
+        if (!same_method(hs[i]->plan, hs[0]->plan)) return OF_EINVAL;
         if (!I1s[i] && !hs[i]->has_prev) return OF_ESTATE;
         if (hs[i]->device != hs[0]->device) return OF_EINVAL;
         for (int j = 0; j < i; ++j)
@@ -140,6 +141,7 @@ static int build_batch(int32_t n, const of_handle *hs, const void *const *I1s, c
         bp.flow[0] = h->flow[0];
         bp.flow[1] = h->flow[1];
         bp.status = h->status;
+        bp.hess = h->hess;
         bp.first_image = I1s[i] ? 0 : 1;
         for (int l = 0; l < L; ++l) {
             bp.H[l] = h->lay.H[l];
@@ -300,8 +302,29 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
             if ((e = launch_phase_pyr(Q, first, p0.in_format, p0.storage, st)) != cudaSuccess) return e;
         }
         // iterations, coarsest level first; flow buffers ping-pong
+        const bool i1grad = (p0.flags & OF_FLAG_I1GRAD) != 0;
         for (int k = 0; k < L * p0.iterations; ++k) {
             const int l = L - 1 - k / p0.iterations, it = k % p0.iterations, cur = k & 1;
+            if (i1grad && it == 0) {
+                // the variant's window matrices of this level, from I1 alone
+                HessPhase Hp;
+                memset(&Hp, 0, sizeof(Hp));
+                Hp.npairs = m;
+                for (int i = 0; i < m; ++i) {
+                    HessArgs &h = Hp.a[i];
+                    h.I1 = bp[i].pyr[0] + bp[i].off[l];
+                    h.H = bp[i].H[l];
+                    h.W = bp[i].W[l];
+                    h.pitch = bp[i].pitch[l];
+                    h.hess = bp[i].hess;
+                    h.hess_pitch = bp[i].pitch[l];
+                    h.tiles_x = (h.W + LK_TW - 1) / LK_TW;
+                    h.tiles = h.tiles_x * ((h.H + LK_TH - 1) / LK_TH);
+                    Hp.prefix[i + 1] = Hp.prefix[i] + h.tiles;
+                }
+                if ((e = launch_phase_hess(Hp, level_elem(p0, l), p0.radius, t.generic_sums != 0, st)) != cudaSuccess)
+                    return e;
+            }
             IterPhase I;
             memset(&I, 0, sizeof(I));
             I.npairs = m;
@@ -334,15 +357,29 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
                 a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
                 a.tiles = a.tiles_x * ((a.H + LK_TH - 1) / LK_TH);
                 a.status = bp[i].status;
-                a.stage_i2 = stage;
+                a.stage_i2 = i1grad ? 0 : stage;
+                a.hess = bp[i].hess;
+                a.hess_pitch = bp[i].pitch[l];
                 I.prefix[i + 1] = I.prefix[i] + a.tiles;
             }
-            if ((e = launch_phase_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, st)) !=
-                cudaSuccess)
-                return e;
+            e = i1grad ? launch_phase_i1_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, st)
+                       : launch_phase_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, st);
+            if (e != cudaSuccess) return e;
         }
     }
     return cudaSuccess;
+}
+
+// The variant with the first image's gradient runs as phase launches only (it has no
+// persistent form) and gathers its 4 taps (no staging).
+static Tuning effective(const of_plan &p0, Tuning t)
+{
+    if (p0.flags & OF_FLAG_I1GRAD) {
+        t.phased = 1;
+        t.blocks_per_sm = 0;
+        t.stage_i2 = 0;
+    }
+    return t;
 }
 
 static int commit_state(int32_t n, const of_handle *hs, const BatchBuild &b, cudaStream_t st)
@@ -405,7 +442,7 @@ int batch_run_slot(BatchSlot &slot, int32_t n, const of_handle *hs, const void *
     const size_t bar_off = bar_offset(b);
     memcpy(slot.host, b.pairs.data(), pairs_bytes);
     memcpy(slot.host + pairs_bytes, b.prefix.data(), prefix_bytes);
-    const Tuning t = tuning_for(p0, batch_size_class(n, hs));
+    const Tuning t = effective(p0, tuning_for(p0, batch_size_class(n, hs)));
     if (t.phased) {
         if (enqueue_phased(b.pairs, p0, t, st) != cudaSuccess || cudaEventRecord(slot.done, st) != cudaSuccess)
             return OF_ECUDA;
@@ -443,9 +480,11 @@ namespace of {
 
 // One batched launch with an explicit tuning, through the cache of captured launches.
 int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s, float *const *us,
-              float *const *vs, cudaStream_t st, const Tuning &t)
+              float *const *vs, cudaStream_t st, const Tuning &t_in)
 {
     if (n == 0) return OF_OK;
+    if (!hs || !hs[0]) return OF_EINVAL;
+    const Tuning t = effective(hs[0]->plan, t_in);
     BatchBuild b;
     int rc = build_batch(n, hs, I1s, I2s, us, vs, b);
     if (rc) return rc;
@@ -457,7 +496,8 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
         memcpy(k, b.pairs.data(), pairs_bytes);
         memcpy(k + pairs_bytes, b.prefix.data(), prefix_bytes);
         memcpy(k + pairs_bytes + prefix_bytes, &st, sizeof(st));
-        const int extra[6] = {p0.radius, (int)(p0.iterations * 8 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD))),
+        const int extra[6] = {p0.radius,
+                              (int)(p0.iterations * 16 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD))),
                               hs[0]->device, t.generic_sums, t.stage_i2, t.blocks_per_sm + 256 * t.phased};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
@@ -582,8 +622,7 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
     for (int i = 0; i < n; ++i) {
         if (!hs[i] || !hI2s[i] || !hus[i] || !hvs[i] || !dI2s[i] || !dus[i] || !dvs[i] || (hI1s[i] && !dI1s[i]))
             return OF_EINVAL;
-        if (!same_method(hs[i]->plan, hs[0]->plan) || (hs[i]->plan.flags & OF_FLAG_I1GRAD) ||
-            hs[i]->device != hs[0]->device)
+        if (!same_method(hs[i]->plan, hs[0]->plan) || hs[i]->device != hs[0]->device)
             return OF_EINVAL;
         if (!hI1s[i] && !hs[i]->has_prev) return OF_ESTATE;
     }

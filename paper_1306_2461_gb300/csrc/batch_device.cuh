@@ -22,6 +22,7 @@ struct BatchPair {
     char *pyr[2];                       // pyramid slots of the first and second image
     float2 *flow[2];                    // ping-pong flow buffers
     int *status;                        // the handle's device status word
+    float4 *hess;                       // window matrices of the first-image-gradient variant (or NULL)
     int32_t first_image;                // 0: build both pyramids, 1: only the second
     int32_t H[MAX_LEVELS], W[MAX_LEVELS], pitch[MAX_LEVELS];
     uint64_t off[MAX_LEVELS];

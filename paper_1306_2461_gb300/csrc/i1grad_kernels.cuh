@@ -49,11 +49,8 @@ template <int R> __device__ __forceinline__ int i1_rowlen(int RW)
 
 // Window matrix of one level: (Sa, Sb, Sc, 0) at every pixel of one output tile.
 template <typename T, int R>
-__global__ void __launch_bounds__(LK_THREADS) i1_hess_kernel(HessArgs a, int r)
+__device__ __forceinline__ void i1_hess_tile(const HessArgs &a, int tile, int r, float *smem)
 {
-    extern __shared__ float4 smem4[];
-    float *smem = reinterpret_cast<float *>(smem4);
-    const int tile = blockIdx.x;
     const int tyi = tile / a.tiles_x;
     const int ty0 = tyi * LK_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
     const T *I1 = static_cast<const T *>(a.I1);
@@ -110,11 +107,8 @@ __global__ void __launch_bounds__(LK_THREADS) i1_hess_kernel(HessArgs a, int r)
 
 // One iteration of the variant on one output tile.
 template <typename T, int R>
-__global__ void __launch_bounds__(LK_THREADS, 4) i1_iter_kernel(IterArgs a, int r, float fp64_cond)
+__device__ __forceinline__ void i1_iter_tile(const IterArgs &a, int tile, int r, float fp64_cond, float *smem)
 {
-    extern __shared__ float4 smem4[];
-    float *smem = reinterpret_cast<float *>(smem4);
-    const int tile = blockIdx.x;
     const int tyi = tile / a.tiles_x;
     const int ty0 = tyi * LK_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
     const T *I1 = static_cast<const T *>(a.I1);
@@ -201,6 +195,38 @@ __global__ void __launch_bounds__(LK_THREADS, 4) i1_iter_kernel(IterArgs a, int 
             }
         }
     }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(LK_THREADS) i1_hess_kernel(HessArgs a, int r)
+{
+    extern __shared__ float4 smem4[];
+    i1_hess_tile<T, R>(a, blockIdx.x, r, reinterpret_cast<float *>(smem4));
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(LK_THREADS, 4) i1_iter_kernel(IterArgs a, int r, float fp64_cond)
+{
+    extern __shared__ float4 smem4[];
+    i1_iter_tile<T, R>(a, blockIdx.x, r, fp64_cond, reinterpret_cast<float *>(smem4));
+}
+
+// The same over the tiles of up to PHASE_PAIRS pairs (batched form).
+template <typename T, int R>
+__global__ void __launch_bounds__(LK_THREADS) phase_hess_kernel(const __grid_constant__ HessPhase P, int r)
+{
+    extern __shared__ float4 smem4[];
+    const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
+    i1_hess_tile<T, R>(P.a[p], blockIdx.x - P.prefix[p], r, reinterpret_cast<float *>(smem4));
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(LK_THREADS, 4)
+phase_i1_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
+{
+    extern __shared__ float4 smem4[];
+    const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
+    i1_iter_tile<T, R>(P.a[p], blockIdx.x - P.prefix[p], r, fp64_cond, reinterpret_cast<float *>(smem4));
 }
 
 }  // namespace of

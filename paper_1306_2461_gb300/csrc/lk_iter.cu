@@ -56,6 +56,29 @@ cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool gen
     }
 }
 
+#define OF_CASE_PHH(R) \
+    case R: return phase_hess_launch<R>(P, elem, radius, s);
+cudaError_t launch_phase_hess(const HessPhase &P, int elem, int radius, bool generic, cudaStream_t s)
+{
+    if (generic) return phase_hess_launch<0>(P, elem, radius, s);
+    switch (radius) {
+        OF_RADII(OF_CASE_PHH)
+    default: return phase_hess_launch<0>(P, elem, radius, s);
+    }
+}
+
+#define OF_CASE_PHI(R) \
+    case R: return phase_i1_launch<R>(P, elem, radius, fp64_cond, s);
+cudaError_t launch_phase_i1_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond,
+                                 cudaStream_t s)
+{
+    if (generic) return phase_i1_launch<0>(P, elem, radius, fp64_cond, s);
+    switch (radius) {
+        OF_RADII(OF_CASE_PHI)
+    default: return phase_i1_launch<0>(P, elem, radius, fp64_cond, s);
+    }
+}
+
 #define OF_CASE_BK(R) \
     case R: return batch_kernel_ptr<R>(in_format, storage);
 void *batch_kernel_for(int in_format, int storage, int radius)

@@ -130,6 +130,7 @@ template <typename A> struct Phase {
 using IterPhase = Phase<IterArgs>;
 using PyrPhase = Phase<PyrArgs>;
 using ZnPhase = Phase<ZnArgs>;
+using HessPhase = Phase<HessArgs>;
 static_assert(sizeof(IterPhase) <= 32000 && sizeof(PyrPhase) <= 32000, "kernel parameters are limited to 32 KB");
 
 // Tile shapes.
@@ -169,6 +170,10 @@ cudaError_t launch_i1_iter(const IterArgs &a, int elem, int radius, float fp64_c
 cudaError_t launch_phase_pyr(const PyrPhase &P, bool first, int in_format, int storage, cudaStream_t s);
 cudaError_t launch_phase_zn(const ZnPhase &P, int in_format, int storage, cudaStream_t s);
 cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond, cudaStream_t s);
+// The first-image-gradient variant: window matrices of one level, then its iterations.
+cudaError_t launch_phase_hess(const HessPhase &P, int elem, int radius, bool generic, cudaStream_t s);
+cudaError_t launch_phase_i1_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond,
+                                 cudaStream_t s);
 void *batch_kernel_for(int in_format, int storage, int radius);
 size_t batch_smem_bytes(int radius, bool stage_i2);
 void *batch_kernel_generic(int in_format, int storage);   // the run-time-radius kernel
@@ -182,6 +187,8 @@ template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float
 template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
 template <int R> cudaError_t i1h_launch(const HessArgs &a, int elem, int r, cudaStream_t s);
 template <int R> cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, cudaStream_t s);
+template <int R> cudaError_t phase_hess_launch(const HessPhase &P, int elem, int r, cudaStream_t s);
+template <int R> cudaError_t phase_i1_launch(const IterPhase &P, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> cudaError_t i1_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> void *batch_kernel_ptr(int in_format, int storage);
 template <int R> cudaError_t radius_configure();

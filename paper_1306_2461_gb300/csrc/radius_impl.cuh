@@ -184,6 +184,44 @@ template <int R> cudaError_t i1_launch(const IterArgs &a, int elem, int r, float
     }
 }
 
+template <typename T, int R> static cudaError_t phase_hess_for(const HessPhase &P, int r, cudaStream_t s)
+{
+    phase_hess_kernel<T, R><<<P.prefix[P.npairs], LK_THREADS, sizeof(float) * i1_smem_floats<R>(r, 3), s>>>(P, r);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t phase_hess_launch(const HessPhase &P, int elem, int r, cudaStream_t s)
+{
+    if (P.prefix[P.npairs] == 0) return cudaSuccess;
+    switch (elem) {
+    case ET_U8: return phase_hess_for<uint8_t, R>(P, r, s);
+    case ET_U16: return phase_hess_for<uint16_t, R>(P, r, s);
+    case ET_F32: return phase_hess_for<float, R>(P, r, s);
+    case ET_F16: return phase_hess_for<__half, R>(P, r, s);
+    default: return phase_hess_for<__nv_bfloat16, R>(P, r, s);
+    }
+}
+
+template <typename T, int R>
+static cudaError_t phase_i1_for(const IterPhase &P, int r, float fp64_cond, cudaStream_t s)
+{
+    phase_i1_iter_kernel<T, R><<<P.prefix[P.npairs], LK_THREADS, sizeof(float) * i1_smem_floats<R>(r, 2), s>>>(
+        P, r, fp64_cond);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t phase_i1_launch(const IterPhase &P, int elem, int r, float fp64_cond, cudaStream_t s)
+{
+    if (P.prefix[P.npairs] == 0) return cudaSuccess;
+    switch (elem) {
+    case ET_U8: return phase_i1_for<uint8_t, R>(P, r, fp64_cond, s);
+    case ET_U16: return phase_i1_for<uint16_t, R>(P, r, fp64_cond, s);
+    case ET_F32: return phase_i1_for<float, R>(P, r, fp64_cond, s);
+    case ET_F16: return phase_i1_for<__half, R>(P, r, fp64_cond, s);
+    default: return phase_i1_for<__nv_bfloat16, R>(P, r, fp64_cond, s);
+    }
+}
+
 template <int R> void *batch_kernel_ptr(int in_format, int storage)
 {
     if (in_format == OF_U8) {
@@ -220,6 +258,10 @@ template <int R> cudaError_t radius_configure()
     if ((e = cudaFuncSetAttribute((const void *)i1_hess_kernel<T, R>,                                     \
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess ||     \
         (e = cudaFuncSetAttribute((const void *)i1_iter_kernel<T, R>,                                     \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ib)) != cudaSuccess ||     \
+        (e = cudaFuncSetAttribute((const void *)phase_hess_kernel<T, R>,                                  \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess ||     \
+        (e = cudaFuncSetAttribute((const void *)phase_i1_iter_kernel<T, R>,                               \
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, ib)) != cudaSuccess)       \
         return e;
         OF_SET_I1(uint8_t)
@@ -239,6 +281,8 @@ template cudaError_t lk_launch<OF_RADIUS>(const IterArgs &, int, int, float, cud
 template cudaError_t ws_launch<OF_RADIUS>(const float *, int, int, int, float *, cudaStream_t);
 template cudaError_t i1h_launch<OF_RADIUS>(const HessArgs &, int, int, cudaStream_t);
 template cudaError_t phase_launch<OF_RADIUS>(const IterPhase &, int, int, float, cudaStream_t);
+template cudaError_t phase_hess_launch<OF_RADIUS>(const HessPhase &, int, int, cudaStream_t);
+template cudaError_t phase_i1_launch<OF_RADIUS>(const IterPhase &, int, int, float, cudaStream_t);
 template cudaError_t i1_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template void *batch_kernel_ptr<OF_RADIUS>(int, int);
 template cudaError_t radius_configure<OF_RADIUS>();

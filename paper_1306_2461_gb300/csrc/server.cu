@@ -256,7 +256,7 @@ int of_server_create(const of_server_config *c, of_server_t *out)
     m.storage = c->storage;
     m.fp64_cond = c->fp64_cond;
     m.flags = c->flags & ~OF_FLAG_NO_GRAPH;
-    if (of_plan_validate(&m) != OF_OK || (m.flags & OF_FLAG_I1GRAD)) return OF_EINVAL;
+    if (of_plan_validate(&m) != OF_OK) return OF_EINVAL;
     of_server *s = new (std::nothrow) of_server();
     if (!s) return OF_ENOMEM;
     s->cfg = *c;

@@ -139,6 +139,7 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
     for (int gs = radius_is_specialised(p0.radius) ? 0 : 1; gs <= 1; ++gs)
         for (int sg = 0; sg <= (gs ? 0 : 1); ++sg)
             for (int b : occ) {
+                if ((p0.flags & OF_FLAG_I1GRAD) && (b >= 0 || sg)) continue;   // phase launches, gathered taps only
                 Tuning t;
                 t.generic_sums = gs;
                 t.stage_i2 = sg;

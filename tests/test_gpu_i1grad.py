@@ -120,16 +120,64 @@ def test_noalloc_entry_accepts_the_variant(of):
     assert np.array_equal(v.cpu().numpy().astype(np.float64), va)
 
 
-def test_batch_and_server_refuse_the_variant(of):
+def test_batched_host_and_served_variant_equal_per_pair(of):
+    # the variant through of_compute_batch (with a reused pyramid), of_compute_batch_host
+    # and the serving loop: of_compute's bits
     import torch
-    plan = of.Plan.make(64, 64, 2, 4, 2, bits=8, flags=of.OF_FLAG_I1GRAD)
-    I = to_dev(np.zeros((64, 64), np.uint8))
-    u = torch.empty(64, 64, device="cuda")
-    with of.Flow(plan) as f:
-        with pytest.raises(of.OfError) as ei:
-            of.compute_batch([f], [I], [I], [u], [u.clone()])
-        assert ei.value.status == of.OF_EINVAL
     from paper_1306_2461_gb300 import serve
-    with pytest.raises(of.OfError) as ei:
-        serve.Server(flags=of.OF_FLAG_I1GRAD)
-    assert ei.value.status == of.OF_EINVAL
+    sizes = [(160, 224), (96, 128), (200, 136)]
+    frames = []
+    for k, (H, W) in enumerate(sizes):
+        st = synth.ParticleStream(H, W, seed=60 + k)
+        fr = []
+        for _ in range(3):
+            fr.append(st.frame())
+            st.advance()
+        frames.append(fr)
+    fl = of.OF_FLAG_I1GRAD
+    plans = [of.Plan.make(H, W, 3, 4, 3, bits=12, storage="f16", flags=fl) for H, W in sizes]
+
+    def alone(k, j):
+        with of.Flow(plans[k]) as f:
+            u, v = f.compute(to_dev(frames[k][j - 1]), to_dev(frames[k][j]))
+            torch.cuda.synchronize()
+        return u, v
+
+    flows = [of.Flow(p) for p in plans]
+    of.compute_batch(flows, [to_dev(f[0]) for f in frames], [to_dev(f[1]) for f in frames])
+    ub, vb = of.compute_batch(flows, [None, to_dev(frames[1][1]), None], [to_dev(f[2]) for f in frames])
+    torch.cuda.synchronize()
+    for k in range(3):
+        u1, v1 = alone(k, 2)
+        assert torch.equal(ub[k], u1) and torch.equal(vb[k], v1), k
+    hu = [torch.empty(s_, dtype=torch.float32).pin_memory() for s_ in sizes]
+    hv = [torch.empty(s_, dtype=torch.float32).pin_memory() for s_ in sizes]
+    du = [torch.empty(s_, device="cuda") for s_ in sizes]
+    dv = [torch.empty(s_, device="cuda") for s_ in sizes]
+    hf = [[serve.pinned_frame(x) for x in fr] for fr in frames]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        of.compute_batch_host(flows, [h[0] for h in hf], [h[1] for h in hf], hu, hv,
+                              [to_dev(f[0]) for f in frames], [to_dev(f[1]) for f in frames], du, dv, stream=s)
+    s.synchronize()
+    for k in range(3):
+        u1, v1 = alone(k, 1)
+        assert torch.equal(hu[k], u1.cpu()) and torch.equal(hv[k], v1.cpu()), k
+    with serve.Server(levels=3, radius=4, iterations=3, bits=12, storage="f16", max_batch=8, flags=fl) as srv:
+        sids = [srv.open_stream(H, W) for H, W in sizes]
+        outs = {}
+        for j in range(3):
+            for k, sid in enumerate(sids):
+                outs[(k, j)] = (torch.empty(sizes[k], device="cuda"), torch.empty(sizes[k], device="cuda"))
+                srv.submit(sid, hf[k][j], *outs[(k, j)], tag=10 * k + j)
+        srv.drain()
+        assert all(r["status"] == 0 for r in srv.poll(0))
+    for k in range(3):
+        for j in (1, 2):
+            u1, v1 = alone(k, j)
+            assert torch.equal(outs[(k, j)][0], u1) and torch.equal(outs[(k, j)][1], v1), (k, j)
+    best, cands = of.autotune_batch(flows, [to_dev(f[0]) for f in frames], [to_dev(f[1]) for f in frames], reps=1)
+    assert len(cands) == 2 and all(c["phased"] == 1 and c["stage_i2"] == 0 for c in cands)
+    of.tuning_clear()
+    for f in flows:
+        f.close()
