@@ -711,9 +711,10 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
     return true;
 }
 
-// The iteration tile for radius R (0 = generic, radius r at run time). Returns false
+// The iteration tile for radius R (0 = generic, radius r at run time). MODE: the flow
+// mode when it is known at compile time (-1: read a.mode at run time). Returns false
 // when the block must stop (a staging copy timed out; recorded in *a.status).
-template <typename T, bool NC, int R>
+template <typename T, bool NC, int R, int MODE = -1>
 __device__ __forceinline__ bool lk_tile(const IterArgs &a, int tile, int r, float fp64_cond, float *smem,
                                         uint32_t &phase)
 {
@@ -721,7 +722,7 @@ __device__ __forceinline__ bool lk_tile(const IterArgs &a, int tile, int r, floa
         lk_tile_generic<T, NC>(a, tile, r, fp64_cond, smem);
         return true;
     } else {
-        return lk_tile_fixed<T, NC, R, -1>(a, tile, fp64_cond, smem, phase);
+        return lk_tile_fixed<T, NC, R, MODE>(a, tile, fp64_cond, smem, phase);
     }
 }
 

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>()) lk_iter_kernel
 
 // One iteration of up to PHASE_PAIRS pairs on one level: block b runs tile
 // b - prefix[p] of pair p. The same tile code as lk_iter_kernel, so the same results.
-template <typename T, int R>
+template <typename T, int R, int MODE>
 __global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>())
 phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
 {
@@ -34,7 +34,7 @@ phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
     const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
     uint32_t phase = 0;
     lk_tile_prepare<R>(smem);
-    lk_tile<T, true, R>(P.a[p], blockIdx.x - P.prefix[p], r, fp64_cond, smem, phase);
+    lk_tile<T, true, R, MODE>(P.a[p], blockIdx.x - P.prefix[p], r, fp64_cond, smem, phase);
 }
 
 // The window sums of five given planes, through the same passes as the iteration tile.
@@ -129,12 +129,18 @@ template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, flo
     return cudaGetLastError();
 }
 
+// The flow mode is the same for every pair of a phase: one kernel per mode.
 template <typename T, int R>
 static cudaError_t phase_for(const IterPhase &P, int r, float fp64_cond, cudaStream_t s)
 {
-    const bool stage = P.npairs > 0 && P.a[0].stage_i2 != 0;
-    phase_iter_kernel<T, R><<<P.prefix[P.npairs], LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r, stage), s>>>(
-        P, r, fp64_cond);
+    const bool stage = P.a[0].stage_i2 != 0;
+    const size_t smem = sizeof(float) * lk_tile_smem_floats<R>(r, stage);
+    const int blocks = P.prefix[P.npairs];
+    switch (P.a[0].mode) {
+    case FLOW_ZERO: phase_iter_kernel<T, R, FLOW_ZERO><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
+    case FLOW_SAME: phase_iter_kernel<T, R, FLOW_SAME><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
+    default: phase_iter_kernel<T, R, FLOW_UPSAMPLE><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
+    }
     return cudaGetLastError();
 }
 
@@ -245,11 +251,14 @@ template <int R> cudaError_t radius_configure()
     OF_SET((lk_iter_kernel<float, R>));
     OF_SET((lk_iter_kernel<__half, R>));
     OF_SET((lk_iter_kernel<__nv_bfloat16, R>));
-    OF_SET((phase_iter_kernel<uint8_t, R>));
-    OF_SET((phase_iter_kernel<uint16_t, R>));
-    OF_SET((phase_iter_kernel<float, R>));
-    OF_SET((phase_iter_kernel<__half, R>));
-    OF_SET((phase_iter_kernel<__nv_bfloat16, R>));
+#define OF_SET_PH(T) OF_SET((phase_iter_kernel<T, R, FLOW_ZERO>)); OF_SET((phase_iter_kernel<T, R, FLOW_SAME>)); \
+    OF_SET((phase_iter_kernel<T, R, FLOW_UPSAMPLE>))
+    OF_SET_PH(uint8_t);
+    OF_SET_PH(uint16_t);
+    OF_SET_PH(float);
+    OF_SET_PH(__half);
+    OF_SET_PH(__nv_bfloat16);
+#undef OF_SET_PH
     OF_SET((window_sums_kernel<R>));
     {
         const int r = R == 0 ? MAX_RADIUS : R;
