@@ -2,6 +2,8 @@
 // kernel: one pyramid-reduction tile and one Gauss-Newton iteration tile.
 #pragma once
 
+#include <float.h>
+
 #include <climits>
 
 #include "async_copy.cuh"
@@ -295,8 +297,9 @@ __device__ __forceinline__ void box_vsum(const float *S, int RH, int r, int ty, 
 }
 
 // Solve [a b; b c] x = [d; e]. Returns false (keep the estimate) when tr <= 0 or
-// det <= 1e-6 tr^2. Pixels with tr^2/det above fp64_cond (or det <= 0) are solved in
-// FP64 from the FP32 sums; fp64_cond == 0 keeps everything in FP32.
+// det <= 1e-6 tr^2. Pixels with tr^2/det above fp64_cond (or det <= 0) form the
+// determinant and the numerators in FP64 from the FP32 sums; fp64_cond == 0 keeps
+// everything in FP32.
 __device__ __forceinline__ bool solve2(const float s[5], float fp64_cond, float &xu, float &xv)
 {
     const float a = s[0], b = s[1], c = s[2], d = s[3], e = s[4];
@@ -304,11 +307,16 @@ __device__ __forceinline__ bool solve2(const float s[5], float fp64_cond, float 
     if (!(tr > 0.0f)) return false;
     const float det = fmaf(a, c, -__fmul_rn(b, b));
     if (fp64_cond > 0.0f && !(det * fp64_cond > tr * tr)) {
+        // ill-conditioned: the determinant and the numerators, where the cancellation
+        // is, in FP64 from the FP32 sums (the products are exact, one rounding each);
+        // the final divisions in FP32
         const double A = a, B = b, C = c, D = d, E = e;
-        const double T = A + C, dt = A * C - B * B;
+        const double T = A + C, dt = fma(A, C, -__dmul_rn(B, B));
         if (!(dt > 1e-6 * T * T)) return false;
-        xu = (float)((C * D - B * E) / dt);
-        xv = (float)((A * E - B * D) / dt);
+        const float fdt = (float)dt;
+        if (!(fdt >= FLT_MIN)) return false;
+        xu = __fdiv_rn((float)fma(C, D, -__dmul_rn(B, E)), fdt);
+        xv = __fdiv_rn((float)fma(A, E, -__dmul_rn(B, D)), fdt);
         return true;
     }
     if (!(det > 1e-6f * tr * tr)) return false;
