@@ -192,3 +192,32 @@ def test_host_buffer_pipeline_equals_device_batch(of, chunk):
                               dI1[:1] * 2, dI2[:1] * 2, du[:1] * 2, dv[:1] * 2, stream=s)
     for f in fa + fb:
         f.close()
+
+
+def test_more_pairs_than_one_phase_launch_holds(of):
+    # 70 small pairs: each phase is split into launches of at most 64 pairs; every
+    # field equals of_compute's, including pairs that reuse their previous pyramid
+    import torch
+    n = 70
+    rng = np.random.default_rng(5)
+    sizes = [(int(rng.integers(24, 96)), int(rng.integers(24, 96))) for _ in range(n)]
+    frames = []
+    for k, (H, W) in enumerate(sizes):
+        st = synth.ParticleStream(H, W, seed=100 + k)
+        fr = []
+        for _ in range(3):
+            fr.append(st.frame())
+            st.advance()
+        frames.append(fr)
+    plans = [of.Plan.make(H, W, 2, 3, 2, bits=12, storage="f16") for H, W in sizes]
+    flows = [of.Flow(p) for p in plans]
+    of.compute_batch(flows, [to_dev(f[0]) for f in frames], [to_dev(f[1]) for f in frames])
+    reuse = [None if k % 3 == 0 else to_dev(frames[k][1]) for k in range(n)]
+    ub, vb = of.compute_batch(flows, reuse, [to_dev(f[2]) for f in frames])
+    torch.cuda.synchronize()
+    assert all(f.sync_status() == of.OF_OK for f in flows)
+    for k in range(n):
+        u1, v1 = single(of, plans[k], to_dev(frames[k][1]), to_dev(frames[k][2]))
+        assert torch.equal(ub[k], u1) and torch.equal(vb[k], v1), k
+    for f in flows:
+        f.close()
