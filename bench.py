@@ -357,12 +357,14 @@ def main():
         "config": {"workload": WORKLOAD, "H": H, "W": W, "bits": BITS, "levels": LEVELS, "radius": RADIUS,
                    "iterations": ITERS, "pairs_per_step": B, "distinct_pairs": DISTINCT,
                    "form": "batched (of_compute_batch), one CUDA graph replay per step",
-                   "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased")}
+                   "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased",
+                                                               "prefetch")}
                               if tuning else "default (autotuner off)"),
                    "l2": "no flush: per-step working set ~%.1f GB >> 129 MB L2" % (
                        B * (of.workspace_bytes(plan16) + 4 * H * W) / 1e9),
                    "parallelism": f"replicas x{world}"},
-        "autotune_candidates_ms": ([[c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"], round(c["ms"], 3)]
+        "autotune_candidates_ms": ([[c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"], c["prefetch"],
+                                     round(c["ms"], 3)]
                                     for c in tuning["candidates"]] if tuning else None),
         "latency_ms": {"step_p50": percentile(step_ms, 50), "step_p99": percentile(step_ms, 99),
                        "step_max": max(step_ms)},

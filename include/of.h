@@ -167,7 +167,7 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  * batch shape has the same results to within the stated tolerances whichever tuning
  * runs it; with grouped sums (generic_sums == 0) they are the results of of_compute bit
  * for bit. Without a table entry a batch runs {generic_sums 0, stage_i2 0,
- * blocks_per_sm 0, phased 1}. A tuning:
+ * blocks_per_sm 0, phased 1, prefetch 1}. A tuning:
  *   generic_sums   1: per-output window sums of the run-time-radius kernel;
  *                  0: grouped sums of the kernel specialised for the radius
  *   stage_i2       1: stage I2 footprints in shared memory (specialised kernel only)
@@ -176,6 +176,8 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  *                  pairs' tiles, the pairs' arguments passed as kernel parameters, in
  *                  place of the one persistent launch with grid barriers (then
  *                  blocks_per_sm must be 0)
+ *   prefetch       phase launches: each iteration block warms L2 with the rows the block
+ *                  prefetch x (number of SMs) tiles later will read first (0: off, <= 16)
  *   ms             measured milliseconds per batch (of_autotune_batch output only)
  * The process-wide table is keyed by the method (in_format, storage, radius, levels,
  * iterations, OF_FLAG_ZNSSD) and a size class, round(log2(mean level-0 pixels per pair)).
@@ -185,6 +187,7 @@ typedef struct of_tuning {
     int32_t stage_i2;
     int32_t blocks_per_sm;
     int32_t phased;
+    int32_t prefetch;
     float ms;
 } of_tuning;
 

@@ -68,7 +68,7 @@ def load(path: str | None = None) -> int:
     for ent in data.values():
         b = ent["best"]
         of.tuning_set(_plan_of(ent["method"]), ent["size_class"], b["generic_sums"], b["stage_i2"],
-                      b["blocks_per_sm"], b.get("phased", 0))
+                      b["blocks_per_sm"], b.get("phased", 0), b.get("prefetch", 0))
     return len(data)
 
 

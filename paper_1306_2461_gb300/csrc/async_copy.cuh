@@ -19,6 +19,13 @@ __device__ __forceinline__ unsigned long long gtimer_ns()
     return t;
 }
 
+// Warm L2 with `bytes` bytes at p (both multiples of 16, inside one allocation): a hint,
+// nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

@@ -247,6 +247,11 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
     const int L = p0.levels;
     const bool zn = (p0.flags & OF_FLAG_ZNSSD) != 0;
     const int32_t stage = (!t.generic_sums && ((p0.flags & OF_FLAG_STAGE_I2) || t.stage_i2)) ? 1 : 0;
+    // L2 prefetch distance of the iteration launches: t.prefetch blocks per SM ahead
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int32_t prefetch_ahead = sms * t.prefetch;
     cudaError_t e;
     for (int g0 = 0; g0 < n; g0 += PHASE_PAIRS) {
         const int m = n - g0 < PHASE_PAIRS ? n - g0 : PHASE_PAIRS;
@@ -328,6 +333,7 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
             IterPhase I;
             memset(&I, 0, sizeof(I));
             I.npairs = m;
+            I.ahead = prefetch_ahead;
             for (int i = 0; i < m; ++i) {
                 IterArgs &a = I.a[i];
                 a.I1 = bp[i].pyr[0] + bp[i].off[l];
@@ -498,7 +504,8 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
         memcpy(k + pairs_bytes + prefix_bytes, &st, sizeof(st));
         const int extra[6] = {p0.radius,
                               (int)(p0.iterations * 16 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD))),
-                              hs[0]->device, t.generic_sums, t.stage_i2, t.blocks_per_sm + 256 * t.phased};
+                              hs[0]->device, t.generic_sums, t.stage_i2,
+                              t.blocks_per_sm + 256 * t.phased + 65536 * t.prefetch};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
 

@@ -124,6 +124,7 @@ constexpr int ZN_EPS = 1;             // added to the local variance (counts squ
 constexpr int PHASE_PAIRS = 64;
 template <typename A> struct Phase {
     int32_t npairs;
+    int32_t ahead;                      // iteration phases: warm L2 for tile b + ahead (0: off)
     int32_t prefix[PHASE_PAIRS + 1];
     A a[PHASE_PAIRS];
 };

@@ -53,6 +53,24 @@ __device__ __forceinline__ int phase_pair(const int32_t *prefix, int n, int b)
     return lo;
 }
 
+// L2 prefetch of row `slot` of the rectangle [y0, y1) x [x0, x1) of a pitched image
+// (elements of `elem` bytes), clamped to the image. Rows of the pyramid and flow buffers
+// start 16-byte aligned and span pitch * elem bytes, a multiple of 16, so the widened
+// range stays inside the row.
+__device__ __forceinline__ void prefetch_row(const void *base, int pitch, int elem, int H, int W, int y0, int y1,
+                                             int x0, int x1, int slot)
+{
+    y0 = max(y0, 0);
+    y1 = min(y1, H);
+    x0 = max(x0, 0);
+    x1 = min(x1, W);
+    if (x0 >= x1 || slot < 0 || slot >= y1 - y0) return;
+    const char *row = static_cast<const char *>(base) + (size_t)(y0 + slot) * pitch * elem;
+    const uintptr_t s = reinterpret_cast<uintptr_t>(row + (size_t)x0 * elem) & ~uintptr_t(15);
+    const uintptr_t e = (reinterpret_cast<uintptr_t>(row + (size_t)x1 * elem) + 15) & ~uintptr_t(15);
+    prefetch_l2(reinterpret_cast<const void *>(s), (uint32_t)(e - s));
+}
+
 // [1 4 6 4 1] . (a, b, c, d, e), with its roundings fixed: (a + e) + 4 (b + d) + 6 c.
 __device__ __forceinline__ float binom5(float a, float b, float c, float d, float e)
 {

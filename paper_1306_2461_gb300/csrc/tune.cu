@@ -41,7 +41,7 @@ bool valid(const Tuning &t)
 {
     return t.generic_sums >= 0 && t.generic_sums <= 1 && t.stage_i2 >= 0 && t.stage_i2 <= 1 && t.blocks_per_sm >= 0 &&
            t.blocks_per_sm <= 64 && t.phased >= 0 && t.phased <= 1 && !(t.generic_sums && t.stage_i2) &&
-           !(t.phased && t.blocks_per_sm);
+           !(t.phased && t.blocks_per_sm) && t.prefetch >= 0 && t.prefetch <= 16;
 }
 
 void to_c(const Tuning &t, float ms, of_tuning *o)
@@ -50,6 +50,7 @@ void to_c(const Tuning &t, float ms, of_tuning *o)
     o->stage_i2 = t.stage_i2;
     o->blocks_per_sm = t.blocks_per_sm;
     o->phased = t.phased;
+    o->prefetch = t.prefetch;
     o->ms = ms;
 }
 
@@ -107,6 +108,7 @@ int of_tuning_set(const of_plan *method, int32_t size_class, const of_tuning *t)
     v.stage_i2 = t->stage_i2;
     v.blocks_per_sm = t->blocks_per_sm;
     v.phased = t->phased;
+    v.prefetch = t->prefetch;
     if (!valid(v)) return OF_EINVAL;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_table[key_of(*method, size_class)] = v;
@@ -132,10 +134,11 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
     const of_plan &p0 = hs[0]->plan;
     // candidates: the grouped fixed-radius sums (gathered or staged I2) when the radius
     // has a specialised kernel, the per-output sums of the run-time-radius kernel; each
-    // as phase launches, and as the persistent launch at full occupancy and at 2 and 1
-    // blocks per SM
+    // as phase launches with an L2 prefetch 1, 0 or 3 blocks per SM ahead, and as the
+    // persistent launch at full occupancy and at 2 and 1 blocks per SM
     std::vector<Tuning> cand;
-    const int occ[4] = {-1, 0, 2, 1};   // -1: phase launches
+    const int occ[6] = {-1, -2, -3, 0, 2, 1};   // < 0: phase launches with prefetch pf_of[-1 - b]
+    const int pf_of[3] = {1, 0, 3};
     for (int gs = radius_is_specialised(p0.radius) ? 0 : 1; gs <= 1; ++gs)
         for (int sg = 0; sg <= (gs ? 0 : 1); ++sg)
             for (int b : occ) {
@@ -145,6 +148,7 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
                 t.stage_i2 = sg;
                 t.phased = b < 0 ? 1 : 0;
                 t.blocks_per_sm = b < 0 ? 0 : b;
+                t.prefetch = b < 0 ? pf_of[-1 - b] : 0;
                 cand.push_back(t);
             }
     cudaEvent_t e0 = nullptr, e1 = nullptr;

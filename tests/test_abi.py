@@ -94,18 +94,21 @@ def test_tuning_table_host_calls(of):
     m = of.Plan.make(64, 64, 3, 4, 5, bits=12, storage="f16")
     of.tuning_clear()
     assert of.tuning_get(m, 20) is None
-    of.tuning_set(m, 20, generic_sums=0, stage_i2=1, blocks_per_sm=2)
+    of.tuning_set(m, 20, generic_sums=0, stage_i2=1, blocks_per_sm=2, phased=0, prefetch=0)
     t = of.tuning_get(m, 20)
-    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"]) == (0, 1, 2)
+    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"], t["phased"]) == (0, 1, 2, 0)
     assert of.tuning_get(m, 19) is None                                   # another size class
     assert of.tuning_get(of.Plan.make(64, 64, 3, 4, 4, bits=12, storage="f16"), 20) is None   # another method
     with pytest.raises(of.OfError):
         of.tuning_set(m, 20, generic_sums=1, stage_i2=1)                  # staging needs the grouped kernel
     with pytest.raises(of.OfError):
-        of.tuning_set(m, 20, blocks_per_sm=-1)
+        of.tuning_set(m, 20, blocks_per_sm=-1, phased=0)
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, prefetch=17)
     with pytest.raises(of.OfError):
         of.tuning_set(m, 20, blocks_per_sm=2, phased=1)                   # occupancy is a persistent-launch knob
-    of.tuning_set(m, 20, phased=1)
-    assert of.tuning_get(m, 20)["phased"] == 1
+    of.tuning_set(m, 20)
+    t = of.tuning_get(m, 20)
+    assert (t["phased"], t["prefetch"]) == (1, 1)
     of.tuning_clear()
     assert of.tuning_get(m, 20) is None

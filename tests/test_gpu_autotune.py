@@ -43,13 +43,14 @@ def test_every_candidate_matches_the_per_pair_path(of, oracle_mod):
     torch.cuda.synchronize()
     best, cands = of.autotune_batch(flows, I1, I2, reps=2)
     print(best, cands)
-    assert len(cands) == 12 and best["ms"] == min(c["ms"] for c in cands)
+    assert len(cands) == 18 and best["ms"] == min(c["ms"] for c in cands)
     sc = of.batch_size_class(flows)
     t = of.tuning_get(flows[0].plan, sc)
-    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"], t["phased"]) == \
-        (best["generic_sums"], best["stage_i2"], best["blocks_per_sm"], best["phased"])
+    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"], t["phased"], t["prefetch"]) == \
+        (best["generic_sums"], best["stage_i2"], best["blocks_per_sm"], best["phased"], best["prefetch"])
     for c in cands:
-        of.tuning_set(flows[0].plan, sc, c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"])
+        of.tuning_set(flows[0].plan, sc, c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"],
+                      c["prefetch"])
         us, vs = of.compute_batch(flows, I1, I2)
         torch.cuda.synchronize()
         for k in range(len(sizes)):
@@ -75,7 +76,7 @@ def test_cache_file_round_trip(of, tmp_path):
     path = str(tmp_path / "tune.json")
     ent = autotune.tune(flows, I1, I2, reps=1, path=path)
     sc = of.batch_size_class(flows)
-    assert ent["size_class"] == sc and len(ent["candidates"]) == 12
+    assert ent["size_class"] == sc and len(ent["candidates"]) == 18
     of.tuning_clear()
     assert of.tuning_get(flows[0].plan, sc) is None
     assert autotune.load(path) == 1
@@ -104,7 +105,7 @@ def test_phase_launches_in_batches_with_reuse_and_in_the_server(of):
     from paper_1306_2461_gb300 import serve
     m = of.Plan.make(64, 64, 3, 4, 3, bits=12, storage="f16")
     for sc in range(8, 27):
-        of.tuning_set(m, sc, phased=1)
+        of.tuning_set(m, sc, phased=1, prefetch=1)
     sizes = [(160, 224), (96, 128), (192, 160)]
     frames = []
     for k, (H, W) in enumerate(sizes):
