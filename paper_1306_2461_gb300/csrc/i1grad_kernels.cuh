@@ -225,6 +225,13 @@ __global__ void __launch_bounds__(LK_THREADS, 4)
 phase_i1_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
 {
     extern __shared__ float4 smem4[];
+    if constexpr (R != 0) {
+        const int t2 = blockIdx.x + P.ahead;
+        if (P.ahead > 0 && t2 < P.prefix[P.npairs]) {
+            const int q = phase_pair(P.prefix, P.npairs, t2);
+            prefetch_tile<T, -1>(P.a[q], t2 - P.prefix[q], R);
+        }
+    }
     const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
     i1_iter_tile<T, R>(P.a[p], blockIdx.x - P.prefix[p], r, fp64_cond, reinterpret_cast<float *>(smem4));
 }

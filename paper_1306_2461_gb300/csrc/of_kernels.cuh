@@ -71,6 +71,35 @@ __device__ __forceinline__ void prefetch_row(const void *base, int pitch, int el
     prefetch_l2(reinterpret_cast<const void *>(s), (uint32_t)(e - s));
 }
 
+// Warm L2 with what the block that runs iteration tile `tile` will read first: its region
+// (tile + r-pixel halo) of the current estimate (flow mode MODE, or a.mode at run time when
+// MODE < 0), of I1, of I2 widened by PF_MARGIN pixels for the displacement, and of the
+// variant's window matrices (a.hess, when set). Threads [0, 64) take the estimate's rows,
+// [64, 128) I1's, [128, 192) I2's, [192, 256) the window matrices'.
+constexpr int PF_MARGIN = 8;
+template <typename T, int MODE>
+__device__ __forceinline__ void prefetch_tile(const IterArgs &a, int tile, int r)
+{
+    const int tyi = tile / a.tiles_x;
+    const int ty0 = tyi * LK_TH - r, tx0 = (tile - tyi * a.tiles_x) * LK_TW - r;
+    const int ty1 = ty0 + LK_TH + 2 * r, tx1 = tx0 + LK_TW + 2 * r;
+    const int t = threadIdx.x;
+    const int mode = MODE >= 0 ? MODE : a.mode;
+    if (t < 64) {
+        if (mode == FLOW_SAME)
+            prefetch_row(a.fin, a.fin_pitch, 8, a.H, a.W, ty0, ty1, tx0, tx1, t);
+        else if (mode == FLOW_UPSAMPLE)
+            prefetch_row(a.fin, a.fin_pitch, 8, a.Hc, a.Wc, ty0 >> 1, (ty1 >> 1) + 2, tx0 >> 1, (tx1 >> 1) + 2, t);
+    } else if (t < 128) {
+        prefetch_row(a.I1, a.pitch, (int)sizeof(T), a.H, a.W, ty0 - 1, ty1 + 1, tx0 - 1, tx1 + 1, t - 64);
+    } else if (t < 192) {
+        prefetch_row(a.I2, a.pitch, (int)sizeof(T), a.H, a.W, ty0 - PF_MARGIN, ty1 + PF_MARGIN, tx0 - PF_MARGIN,
+                     tx1 + PF_MARGIN, t - 128);
+    } else if (a.hess) {
+        prefetch_row(a.hess, a.hess_pitch, 16, a.H, a.W, ty0 + r, ty1 - r, tx0 + r, tx1 - r, t - 192);
+    }
+}
+
 // [1 4 6 4 1] . (a, b, c, d, e), with its roundings fixed: (a + e) + 4 (b + d) + 6 c.
 __device__ __forceinline__ float binom5(float a, float b, float c, float d, float e)
 {

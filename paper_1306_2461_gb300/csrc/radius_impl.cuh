@@ -25,30 +25,6 @@ __global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>()) lk_iter_kernel
 
 // One iteration of up to PHASE_PAIRS pairs on one level: block b runs tile
 // b - prefix[p] of pair p. The same tile code as lk_iter_kernel, so the same results.
-// Warm L2 with what the block that runs tile t (one wave later) will read first: its
-// region of the current estimate, of I1, and of I2 widened by PF_MARGIN pixels for the
-// displacement. Threads [0, 64) take the estimate's rows, [64, 128) I1's, [128, 256) I2's.
-constexpr int PF_MARGIN = 8;
-template <typename T, int R, int MODE>
-__device__ __forceinline__ void prefetch_tile(const IterArgs &a, int tile)
-{
-    const int tyi = tile / a.tiles_x;
-    const int ty0 = tyi * LK_TH - R, tx0 = (tile - tyi * a.tiles_x) * LK_TW - R;
-    const int ty1 = ty0 + LK_TH + 2 * R, tx1 = tx0 + LK_TW + 2 * R;
-    const int t = threadIdx.x;
-    if (t < 64) {
-        if constexpr (MODE == FLOW_SAME)
-            prefetch_row(a.fin, a.fin_pitch, 8, a.H, a.W, ty0, ty1, tx0, tx1, t);
-        else if constexpr (MODE == FLOW_UPSAMPLE)
-            prefetch_row(a.fin, a.fin_pitch, 8, a.Hc, a.Wc, ty0 >> 1, (ty1 >> 1) + 2, tx0 >> 1, (tx1 >> 1) + 2, t);
-    } else if (t < 128) {
-        prefetch_row(a.I1, a.pitch, (int)sizeof(T), a.H, a.W, ty0, ty1, tx0, tx1, t - 64);
-    } else {
-        prefetch_row(a.I2, a.pitch, (int)sizeof(T), a.H, a.W, ty0 - PF_MARGIN, ty1 + PF_MARGIN, tx0 - PF_MARGIN,
-                     tx1 + PF_MARGIN, t - 128);
-    }
-}
-
 template <typename T, int R, int MODE>
 __global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>())
 phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
@@ -59,7 +35,7 @@ phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
         const int t2 = blockIdx.x + P.ahead;
         if (P.ahead > 0 && t2 < P.prefix[P.npairs]) {
             const int q = phase_pair(P.prefix, P.npairs, t2);
-            prefetch_tile<T, R, MODE>(P.a[q], t2 - P.prefix[q]);
+            prefetch_tile<T, MODE>(P.a[q], t2 - P.prefix[q], R);
         }
     }
     const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
