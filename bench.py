@@ -322,7 +322,7 @@ def main():
 
     extras = {}
     if not args.no_extras:
-        extras = extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows)
+        extras = extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows, world)
 
     # accuracy of the timed configuration on one pair (outside the timed region)
     p0 = src[0]
@@ -402,9 +402,11 @@ def main():
     return 0
 
 
-def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows):
+def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows, world=1):
     """Outside the headline timed region: the plain FP32 single-pair form (the comparison
-    the target names), and e2e through the C ABI with host buffers."""
+    the target names), the first-image-gradient variant, e2e through the C ABI with host
+    buffers (whole job over all ranks, like the headline), and the serving loop. The
+    single-pair, variant and serving legs are this rank's GPU alone."""
     out = {}
     K = max(args.steps, 20)
     # plain FP32 single pair, one of_compute (graph replay) per field; the same at FP16
@@ -482,15 +484,17 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
             for _ in range(3):
                 fn()
             stream.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for _ in range(Ke):
                 fn()
             b.record(stream)
             stream.synchronize()
-        ms = a.elapsed_time(b)
-        out[key] = {"value": B * Ke / (ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": B * 2 * H * W * 2,
-                    "d2h_bytes_per_step": B * 2 * H * W * 4, "steps": Ke, "path": path}
+        ms, fields = aggregate(a.elapsed_time(b), B * Ke, world)
+        out[key] = {"value": fields / (ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": world * B * 2 * H * W * 2,
+                    "d2h_bytes_per_step": world * B * 2 * H * W * 4, "steps": Ke, "path": path}
     out["serving"] = serving_leg(torch, synth)
     return out
 
