@@ -324,7 +324,7 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
                     h.hess = bp[i].hess;
                     h.hess_pitch = bp[i].pitch[l];
                     h.tiles_x = (h.W + LK_TW - 1) / LK_TW;
-                    h.tiles = h.tiles_x * ((h.H + LK_TH - 1) / LK_TH);
+                    h.tiles = h.tiles_x * ((h.H + I1_TH - 1) / I1_TH);
                     Hp.prefix[i + 1] = Hp.prefix[i] + h.tiles;
                 }
                 if ((e = launch_phase_hess(Hp, level_elem(p0, l), p0.radius, t.generic_sums != 0, st)) != cudaSuccess)
@@ -361,7 +361,8 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
                     a.fout_pitch = bp[i].pitch[l];
                 }
                 a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
-                a.tiles = a.tiles_x * ((a.H + LK_TH - 1) / LK_TH);
+                const int th = i1grad ? I1_TH : LK_TH;   // the variant's kernels have their own tile height
+                a.tiles = a.tiles_x * ((a.H + th - 1) / th);
                 a.status = bp[i].status;
                 a.stage_i2 = i1grad ? 0 : stage;
                 a.hess = bp[i].hess;

@@ -28,10 +28,10 @@ __device__ __forceinline__ void i1_grad(const T *I1, int pitch, int H, int W, in
 template <int R> inline __host__ __device__ int i1_smem_floats(int r, int channels)
 {
     if constexpr (R == 0) {
-        const int RH = LK_TH + 2 * r, RW = LK_TW + 2 * r;
+        const int RH = I1_TH + 2 * r, RW = LK_TW + 2 * r;
         return channels * (RH * RW + RH * LK_TW);
     } else {
-        return channels * FixedTile<R>::PLANE;
+        return channels * FixedTile<R, I1_TH>::PLANE;
     }
 }
 
@@ -39,12 +39,12 @@ template <int R> inline __host__ __device__ int i1_smem_floats(int r, int channe
 template <int R> __device__ __forceinline__ int i1_plane(int RH, int RW)
 {
     if constexpr (R == 0) return RH * RW;
-    else return FixedTile<R>::PLANE;
+    else return FixedTile<R, I1_TH>::PLANE;
 }
 template <int R> __device__ __forceinline__ int i1_rowlen(int RW)
 {
     if constexpr (R == 0) return RW;
-    else return FixedTile<R>::RWP;
+    else return FixedTile<R, I1_TH>::RWP;
 }
 
 // Window matrix of one level: (Sa, Sb, Sc, 0) at every pixel of one output tile.
@@ -52,10 +52,10 @@ template <typename T, int R>
 __device__ __forceinline__ void i1_hess_tile(const HessArgs &a, int tile, int r, float *smem)
 {
     const int tyi = tile / a.tiles_x;
-    const int ty0 = tyi * LK_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
+    const int ty0 = tyi * I1_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
     const T *I1 = static_cast<const T *>(a.I1);
     const int rr = R == 0 ? r : R;
-    const int RH = LK_TH + 2 * rr, RW = LK_TW + 2 * rr;
+    const int RH = I1_TH + 2 * rr, RW = LK_TW + 2 * rr;
     const int plane = i1_plane<R>(RH, RW);
     const int rowlen = i1_rowlen<R>(RW);
     for (int i = threadIdx.x; i < RH * RW; i += LK_THREADS) {
@@ -79,7 +79,7 @@ __device__ __forceinline__ void i1_hess_tile(const HessArgs &a, int tile, int r,
         float *S = smem + 3 * plane;
         box_hsum<3>(smem, S, RH, RW, r);
         __syncthreads();
-        for (int i = threadIdx.x; i < LK_TH * LK_TW; i += LK_THREADS) {
+        for (int i = threadIdx.x; i < I1_TH * LK_TW; i += LK_THREADS) {
             const int ty = i / LK_TW, tx = i - ty * LK_TW;
             const int y = ty0 + ty, x = tx0 + tx;
             if (y >= a.H || x >= a.W) continue;
@@ -88,13 +88,13 @@ __device__ __forceinline__ void i1_hess_tile(const HessArgs &a, int tile, int r,
             a.hess[(size_t)y * a.hess_pitch + x] = make_float4(s[0], s[1], s[2], 0.0f);
         }
     } else {
-        box_h_inplace<R, 3>(smem);
-        for (int i = threadIdx.x; i < LK_TW * (LK_TH / 4); i += LK_THREADS) {
+        box_h_inplace<R, 3, I1_TH>(smem);
+        for (int i = threadIdx.x; i < LK_TW * (I1_TH / 4); i += LK_THREADS) {
             const int tx = i % LK_TW, g = i / LK_TW;
             const int x = tx0 + tx;
             if (x >= a.W || ty0 + 4 * g >= a.H) continue;
             float s[3][4];
-            box_v4<R, 3>(smem, g, tx, s);
+            box_v4<R, 3, I1_TH>(smem, g, tx, s);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int y = ty0 + 4 * g + j;
@@ -110,12 +110,12 @@ template <typename T, int R>
 __device__ __forceinline__ void i1_iter_tile(const IterArgs &a, int tile, int r, float fp64_cond, float *smem)
 {
     const int tyi = tile / a.tiles_x;
-    const int ty0 = tyi * LK_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
+    const int ty0 = tyi * I1_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
     const T *I1 = static_cast<const T *>(a.I1);
     const T *I2 = static_cast<const T *>(a.I2);
-    const float2 ref = flow_at<true>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + LK_TH / 2, a.H - 1));
+    const float2 ref = flow_at<true>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + I1_TH / 2, a.H - 1));
     const int rr = R == 0 ? r : R;
-    const int RH = LK_TH + 2 * rr, RW = LK_TW + 2 * rr;
+    const int RH = I1_TH + 2 * rr, RW = LK_TW + 2 * rr;
     const int plane = i1_plane<R>(RH, RW);
     const int rowlen = i1_rowlen<R>(RW);
     const int nreg = RH * RW;
@@ -170,7 +170,7 @@ __device__ __forceinline__ void i1_iter_tile(const IterArgs &a, int tile, int r,
         float *S = smem + 2 * plane;
         box_hsum<2>(smem, S, RH, RW, r);
         __syncthreads();
-        for (int i = threadIdx.x; i < LK_TH * LK_TW; i += LK_THREADS) {
+        for (int i = threadIdx.x; i < I1_TH * LK_TW; i += LK_THREADS) {
             const int ty = i / LK_TW, tx = i - ty * LK_TW;
             const int y = ty0 + ty, x = tx0 + tx;
             if (y >= a.H || x >= a.W) continue;
@@ -179,14 +179,14 @@ __device__ __forceinline__ void i1_iter_tile(const IterArgs &a, int tile, int r,
             finish(x, y, s[0], s[1]);
         }
     } else {
-        box_h_inplace<R, 2>(smem);
+        box_h_inplace<R, 2, I1_TH>(smem);
 #pragma unroll 1
-        for (int i = threadIdx.x; i < LK_TW * (LK_TH / 4); i += LK_THREADS) {
+        for (int i = threadIdx.x; i < LK_TW * (I1_TH / 4); i += LK_THREADS) {
             const int tx = i % LK_TW, g = i / LK_TW;
             const int x = tx0 + tx;
             if (x >= a.W || ty0 + 4 * g >= a.H) continue;
             float s[2][4];
-            box_v4<R, 2>(smem, g, tx, s);
+            box_v4<R, 2, I1_TH>(smem, g, tx, s);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int y = ty0 + 4 * g + j;
@@ -204,8 +204,11 @@ __global__ void __launch_bounds__(LK_THREADS) i1_hess_kernel(HessArgs a, int r)
     i1_hess_tile<T, R>(a, blockIdx.x, r, reinterpret_cast<float *>(smem4));
 }
 
+#ifndef OF_I1_MIN_BLOCKS
+#define OF_I1_MIN_BLOCKS 6
+#endif
 template <typename T, int R>
-__global__ void __launch_bounds__(LK_THREADS, 4) i1_iter_kernel(IterArgs a, int r, float fp64_cond)
+__global__ void __launch_bounds__(LK_THREADS, OF_I1_MIN_BLOCKS) i1_iter_kernel(IterArgs a, int r, float fp64_cond)
 {
     extern __shared__ float4 smem4[];
     i1_iter_tile<T, R>(a, blockIdx.x, r, fp64_cond, reinterpret_cast<float *>(smem4));
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(LK_THREADS) phase_hess_kernel(const __grid_con
 }
 
 template <typename T, int R>
-__global__ void __launch_bounds__(LK_THREADS, 4)
+__global__ void __launch_bounds__(LK_THREADS, OF_I1_MIN_BLOCKS)
 phase_i1_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
 {
     extern __shared__ float4 smem4[];
@@ -229,7 +232,7 @@ phase_i1_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond
         const int t2 = blockIdx.x + P.ahead;
         if (P.ahead > 0 && t2 < P.prefix[P.npairs]) {
             const int q = phase_pair(P.prefix, P.npairs, t2);
-            prefetch_tile<T, -1>(P.a[q], t2 - P.prefix[q], R);
+            prefetch_tile<T, -1, I1_TH>(P.a[q], t2 - P.prefix[q], R);
         }
     }
     const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);

@@ -179,7 +179,7 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
             ha.hess = h->hess;
             ha.hess_pitch = L.pitch[l];
             ha.tiles_x = (ha.W + LK_TW - 1) / LK_TW;
-            ha.tiles = ha.tiles_x * ((ha.H + LK_TH - 1) / LK_TH);
+            ha.tiles = ha.tiles_x * ((ha.H + I1_TH - 1) / I1_TH);
             if ((e = launch_i1_hess(ha, level_elem(p, l), p.radius, st)) != cudaSuccess) return e;
         }
         for (int it = 0; it < p.iterations; ++it) {
@@ -212,7 +212,8 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
                 a.fout_pitch = L.pitch[l];
             }
             a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
-            a.tiles = a.tiles_x * ((a.H + LK_TH - 1) / LK_TH);
+            const int th = i1grad ? I1_TH : LK_TH;   // the variant's kernels have their own tile height
+            a.tiles = a.tiles_x * ((a.H + th - 1) / th);
             a.status = h->status;
             a.stage_i2 = (p.flags & OF_FLAG_STAGE_I2) ? 1 : 0;
             if (i1grad) {

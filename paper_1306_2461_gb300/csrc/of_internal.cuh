@@ -136,10 +136,21 @@ static_assert(sizeof(IterPhase) <= 32000 && sizeof(PyrPhase) <= 32000, "kernel p
 
 // Tile shapes.
 constexpr int LK_TW = 64;    // iteration output tile width
+// Iteration output tile: 64 x 20 (measured at the 1024^2, r = 4 batch: 64 x 32 at 3
+// blocks per SM 7.3k fields/s, 64 x 28 and 64 x 24 at 4 blocks 8.1k, 64 x 20 at 5 blocks
+// 8.3k, 64 x 16 at 6 blocks 8.1k). The height can be set at build time (a multiple of 4).
 #ifndef OF_LK_TH
-#define OF_LK_TH 32
+#define OF_LK_TH 20
 #endif
-constexpr int LK_TH = OF_LK_TH;   // iteration output tile height (a multiple of 4)
+constexpr int LK_TH = OF_LK_TH;
+static_assert(LK_TH % 4 == 0, "the vertical box pass takes 4 rows at a time");
+// Output tile height of the first-image-gradient variant's kernels (two product planes,
+// so a taller tile still leaves room for many blocks per SM).
+#ifndef OF_I1_TH
+#define OF_I1_TH 32
+#endif
+constexpr int I1_TH = OF_I1_TH;
+static_assert(I1_TH % 4 == 0, "the vertical box pass takes 4 rows at a time");
 #ifndef OF_LK_THREADS
 #define OF_LK_THREADS 256
 #endif

@@ -77,12 +77,12 @@ __device__ __forceinline__ void prefetch_row(const void *base, int pitch, int el
 // variant's window matrices (a.hess, when set). Threads [0, 64) take the estimate's rows,
 // [64, 128) I1's, [128, 192) I2's, [192, 256) the window matrices'.
 constexpr int PF_MARGIN = 8;
-template <typename T, int MODE>
+template <typename T, int MODE, int TH = LK_TH>
 __device__ __forceinline__ void prefetch_tile(const IterArgs &a, int tile, int r)
 {
     const int tyi = tile / a.tiles_x;
-    const int ty0 = tyi * LK_TH - r, tx0 = (tile - tyi * a.tiles_x) * LK_TW - r;
-    const int ty1 = ty0 + LK_TH + 2 * r, tx1 = tx0 + LK_TW + 2 * r;
+    const int ty0 = tyi * TH - r, tx0 = (tile - tyi * a.tiles_x) * LK_TW - r;
+    const int ty1 = ty0 + TH + 2 * r, tx1 = tx0 + LK_TW + 2 * r;
     const int t = threadIdx.x;
     const int mode = MODE >= 0 ? MODE : a.mode;
     if (t < 64) {
@@ -450,75 +450,68 @@ __device__ __forceinline__ void lk_tile_generic(const IterArgs &a, int tile, int
 // at multiples of 4 in image coordinates (tiles are multiples of 4 wide and high), so
 // the order of the additions depends only on the pixel's position, not on the tiling:
 // the batched and the per-pair launches give the same bits.
-template <int R> struct FixedTile {
+template <int R, int TH = LK_TH> struct FixedTile {
     static_assert(R >= 2, "the grouped box sums need 2R >= 4");
     static constexpr int W = 2 * R + 1;                // window width
     static constexpr int NV4 = (2 * R + 4 + 3) / 4;    // float4 loads for 4 outputs' windows
-    static constexpr int RH = LK_TH + 2 * R;           // region rows (tile + halo)
+    static constexpr int RH = TH + 2 * R;              // region rows (tile + halo)
     static constexpr int RW = LK_TW + 2 * R;           // region columns
     static constexpr int RWP = LK_TW + 4 * NV4 - 4;    // padded row length (>= RW, multiple of 4)
     static constexpr int PLANE = RH * RWP;
     static constexpr int NREG = RH * RW;               // region pixels
     static constexpr int PER = (NREG + LK_THREADS - 1) / LK_THREADS;   // region pixels per thread
-    // I2 staged in shared memory as FP32: the bounding box of every tap the region's
-    // warps read, when it holds at most FBOX floats (else the taps come from global).
-    static constexpr int FBOX = (RW + 10) * (RH + 10);
-    static_assert(PLANE % 2 == 0, "the mbarrier after the planes must be 8-byte aligned");
-    static constexpr int OFF_BAR = 5 * PLANE;                        // 8-byte aligned mbarrier
-    static constexpr int OFF_BOX = OFF_BAR + 2;                      // 4 ints: box bounds
-    static constexpr int OFF_FBOX = OFF_BOX + 4;
-    static constexpr int SMEM_NOSTAGE = OFF_FBOX;                    // launches without I2 staging
-    static constexpr int SMEM_FLOATS = OFF_FBOX + FBOX;
+    // Staging of I2 (a.stage_i2): a window of the tile's region shifted by the tile's
+    // reference flow and widened by STAGE_MARGIN pixels (plus the 4x4 tap footprint and
+    // 16-byte alignment of its rows), in the storage type. WIN_BYTES holds it for 1- and
+    // 2-byte types; a larger window (FP32 storage) is not staged.
+    static constexpr int STAGE_MARGIN = 6;
+    static constexpr int WIN_ROWS = TH + 2 * R + 2 * STAGE_MARGIN + 4;
+    static constexpr int WIN_BYTES = WIN_ROWS * 2 * (LK_TW + 2 * R + 2 * STAGE_MARGIN + 4 + 16);
+    static_assert(PLANE % 4 == 0, "the barrier and the window after the planes must be 16-byte aligned");
+    static constexpr int OFF_BAR = 5 * PLANE;       // 8-byte mbarrier
+    static constexpr int OFF_WIN = OFF_BAR + 4;     // 16-byte aligned staging window
+    static constexpr int SMEM_NOSTAGE = OFF_WIN;    // launches without I2 staging
+    static constexpr int SMEM_FLOATS = OFF_WIN + (WIN_BYTES + 15) / 16 * 4;
 #ifndef OF_LK_MIN_BLOCKS
-#define OF_LK_MIN_BLOCKS 3
+#define OF_LK_MIN_BLOCKS 5   // resident blocks per SM the fixed-radius kernels are compiled for (R <= 6)
 #endif
     static constexpr int MIN_BLOCKS = R <= 6 ? OF_LK_MIN_BLOCKS : 2;
 };
 
 constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's row copies
 
-// Bilinear sample from the staged FP32 box (rows by0.., columns bx0.., row length bw),
-// with the same clamping as bil().
-__device__ __forceinline__ float bil_box(const float *box, int bw, int bx0, int by0, int H, int W, float x, float y)
-{
-    x = fminf(fmaxf(x, 0.0f), (float)(W - 1));
-    y = fminf(fmaxf(y, 0.0f), (float)(H - 1));
-    const float fx = floorf(x), fy = floorf(y);
-    const int x0 = (int)fx, y0 = (int)fy;
-    const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
-    const float ax = x - fx, ay = y - fy;
-    const float *r0 = box + (y0 - by0) * bw - bx0, *r1 = box + (y1 - by0) * bw - bx0;
-    return lerpf(lerpf(r0[x0], r0[x1], ax), lerpf(r1[x0], r1[x1], ax), ay);
-}
-
-// sample_grad() with the taps read from the staged box.
-__device__ __forceinline__ void sample_grad_box(const float *box, int bw, int bx0, int by0, int H, int W, float px,
-                                                float py, float &Iw, float &gx, float &gy)
-{
-    if (px >= 1.0f && py >= 1.0f && px < (float)(W - 2) && py < (float)(H - 2)) {
-        const float fx = floorf(px), fy = floorf(py);
-        const int x0 = (int)fx, y0 = (int)fy;
-        const float ax = px - fx, ay = py - fy;
-        const float *rm = box + (y0 - 1 - by0) * bw + (x0 - bx0);
-        const float *r0 = rm + bw, *r1 = r0 + bw, *r2 = r1 + bw;
-        const float a0 = rm[0], a1 = rm[1];
-        const float bm = r0[-1], b0 = r0[0], b1 = r0[1], b2 = r0[2];
-        const float cm = r1[-1], c0 = r1[0], c1 = r1[1], c2 = r1[2];
-        const float d0 = r2[0], d1 = r2[1];
-        const float top = lerpf(b0, b1, ax), bot = lerpf(c0, c1, ax);
-        Iw = lerpf(top, bot, ay);
-        gx = (lerpf(lerpf(b1, b2, ax), lerpf(c1, c2, ax), ay) - lerpf(lerpf(bm, b0, ax), lerpf(cm, c0, ax), ay)) * 0.5f;
-        gy = (lerpf(bot, lerpf(d0, d1, ax), ay) - lerpf(lerpf(a0, a1, ax), top, ay)) * 0.5f;
-    } else {
-        Iw = bil_box(box, bw, bx0, by0, H, W, px, py);
-        gx = (bil_box(box, bw, bx0, by0, H, W, px + 1.0f, py) - bil_box(box, bw, bx0, by0, H, W, px - 1.0f, py)) * 0.5f;
-        gy = (bil_box(box, bw, bx0, by0, H, W, px, py + 1.0f) - bil_box(box, bw, bx0, by0, H, W, px, py - 1.0f)) * 0.5f;
-    }
-}
-
 template <typename T> __device__ __forceinline__ float ld_smem_elem(const unsigned char *p)
 {
     return ldf<false>(reinterpret_cast<const T *>(p));
+}
+
+// The interior branch of sample_grad with its 12 taps read from the staged window (rows
+// wy0.., columns wx0.., `rowbytes` per row). Returns false, reading nothing, when the
+// 4x4 footprint of (px, py) is not inside both the window and the image's interior.
+template <typename T>
+__device__ __forceinline__ bool sample_grad_win(const unsigned char *win, int rowbytes, int wx0, int wy0, int wx1,
+                                                int wy1, int H, int W, float px, float py, float &Iw, float &gx,
+                                                float &gy)
+{
+    if (!(px >= 1.0f && py >= 1.0f && px < (float)(W - 2) && py < (float)(H - 2))) return false;
+    const float fx = floorf(px), fy = floorf(py);
+    const int x0 = (int)fx, y0 = (int)fy;
+    if (x0 - 1 < wx0 || x0 + 2 >= wx1 || y0 - 1 < wy0 || y0 + 2 >= wy1) return false;
+    const float ax = px - fx, ay = py - fy;
+    constexpr int S = (int)sizeof(T);
+    const unsigned char *rm = win + (y0 - 1 - wy0) * rowbytes + (x0 - wx0) * S;
+    const unsigned char *r0 = rm + rowbytes, *r1 = r0 + rowbytes, *r2 = r1 + rowbytes;
+    const float a0 = ld_smem_elem<T>(rm), a1 = ld_smem_elem<T>(rm + S);
+    const float bm = ld_smem_elem<T>(r0 - S), b0 = ld_smem_elem<T>(r0), b1 = ld_smem_elem<T>(r0 + S),
+                b2 = ld_smem_elem<T>(r0 + 2 * S);
+    const float cm = ld_smem_elem<T>(r1 - S), c0 = ld_smem_elem<T>(r1), c1 = ld_smem_elem<T>(r1 + S),
+                c2 = ld_smem_elem<T>(r1 + 2 * S);
+    const float d0 = ld_smem_elem<T>(r2), d1 = ld_smem_elem<T>(r2 + S);
+    const float top = lerpf(b0, b1, ax), bot = lerpf(c0, c1, ax);
+    Iw = lerpf(top, bot, ay);
+    gx = (lerpf(lerpf(b1, b2, ax), lerpf(c1, c2, ax), ay) - lerpf(lerpf(bm, b0, ax), lerpf(cm, c0, ax), ay)) * 0.5f;
+    gy = (lerpf(bot, lerpf(d0, d1, ax), ay) - lerpf(lerpf(a0, a1, ax), top, ay)) * 0.5f;
+    return true;
 }
 
 // o[j] = sum_{k=0}^{2R} v[j+k], j = 0..3, from v[0 .. 2R+3].
@@ -536,10 +529,10 @@ __device__ __forceinline__ void box4(const float *v, float o[4])
 
 // Horizontal pass, in place: row ry of plane c (c < C) becomes, at columns
 // 0..LK_TW-1, the window sums of the outputs of that row.
-template <int R, int C = 5>
+template <int R, int C = 5, int TH = LK_TH>
 __device__ __forceinline__ void box_h_inplace(float *P)
 {
-    using F = FixedTile<R>;
+    using F = FixedTile<R, TH>;
     constexpr int NG = LK_TW / 4;
     static_assert(32 % NG == 0 && LK_THREADS % 32 == 0, "a row's items must lie in one warp");
     constexpr int NITEMS = F::RH * NG;
@@ -584,10 +577,10 @@ __device__ __forceinline__ void box_h_inplace(float *P)
 }
 
 // Vertical pass for the 4 outputs (rows 4g..4g+3, column tx) of each of C channels.
-template <int R, int C = 5>
+template <int R, int C = 5, int TH = LK_TH>
 __device__ __forceinline__ void box_v4(const float *P, int g, int tx, float s[C][4])
 {
-    using F = FixedTile<R>;
+    using F = FixedTile<R, TH>;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const float *col = P + c * F::PLANE + 4 * g * F::RWP + tx;
@@ -616,83 +609,48 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
 {
     using F = FixedTile<R>;
     float *P = smem;
-    float *fbox = smem + F::OFF_FBOX;
+    unsigned char *win = reinterpret_cast<unsigned char *>(smem + F::OFF_WIN);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + F::OFF_BAR);
-    int *s_box = reinterpret_cast<int *>(smem + F::OFF_BOX);
     const int tyi = tile / a.tiles_x;
     const int ty0 = tyi * LK_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
     const float2 ref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + LK_TH / 2, a.H - 1));
     const T *I1 = static_cast<const T *>(a.I1);
     const T *I2 = static_cast<const T *>(a.I2);
-    if (threadIdx.x == 0) {
-        s_box[0] = INT_MAX;
-        s_box[1] = INT_MIN;
-        s_box[2] = INT_MAX;
-        s_box[3] = INT_MIN;
-    }
-    __syncthreads();   // the previous tile's readers of smem are done; s_box is reset
-    // pass 0: the bounding box of the I2 taps the region's pixels will read
-    int lx0 = INT_MAX, lx1 = INT_MIN, ly0 = INT_MAX, ly1 = INT_MIN;
-#pragma unroll 4
-    for (int i = threadIdx.x; a.stage_i2 && i < F::NREG; i += LK_THREADS) {
-        const int ry = i / F::RW, rx = i - ry * F::RW;
-        const int y = ty0 - R + ry, x = tx0 - R + rx;
-        if ((unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W) {
-            const float2 f = flow_mode<NC, MODE>(a, x, y);
-            const int ix = (int)fminf(fmaxf((float)x + f.x, 0.0f), (float)(a.W - 1));
-            const int iy = (int)fminf(fmaxf((float)y + f.y, 0.0f), (float)(a.H - 1));
-            lx0 = min(lx0, ix - 1);
-            lx1 = max(lx1, ix + 2);
-            ly0 = min(ly0, iy - 1);
-            ly1 = max(ly1, iy + 2);
-        }
-    }
-    lx0 = __reduce_min_sync(0xffffffffu, lx0);
-    lx1 = __reduce_max_sync(0xffffffffu, lx1);
-    ly0 = __reduce_min_sync(0xffffffffu, ly0);
-    ly1 = __reduce_max_sync(0xffffffffu, ly1);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(&s_box[0], lx0);
-        atomicMax(&s_box[1], lx1);
-        atomicMin(&s_box[2], ly0);
-        atomicMax(&s_box[3], ly1);
-    }
-    __syncthreads();
-    const int bx0 = max(s_box[0], 0), bx1 = min(s_box[1], a.W - 1);
-    const int by0 = max(s_box[2], 0), by1 = min(s_box[3], a.H - 1);
-    const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
-    constexpr int E = 16 / (int)sizeof(T);   // elements per 16-byte chunk
-    const int cx0 = bx0 / E, cx1 = bx1 / E;
-    const int rowbytes = (cx1 - cx0 + 1) * 16;
-    const bool staged = a.stage_i2 && bw > 0 && bh > 0 && bw * bh <= F::FBOX && bh * rowbytes <= 5 * F::PLANE * 4;
-    if (staged) {
-        // one round of row copies into the start of the (not yet written) product planes
-        unsigned char *raw = reinterpret_cast<unsigned char *>(P);
-        if (threadIdx.x < 32) {
-            if (threadIdx.x == 0) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, (uint32_t)(bh * rowbytes));
+    __syncthreads();   // the previous tile's readers of smem are done
+    // Staging: the window of I2 around the tile's region displaced by the reference flow,
+    // row by row with bulk copies (raw storage type, 16-byte aligned rows, clamped to the
+    // image's rows and to the padded row length). The window is the same for every thread.
+    int wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0, rowbytes = 0;
+    bool staged = false;
+    if (a.stage_i2) {
+        constexpr int E = 16 / (int)sizeof(T);   // elements per 16-byte chunk
+        const int ox = __float2int_rn(fminf(fmaxf(ref.x, -(float)a.W), (float)a.W));
+        const int oy = __float2int_rn(fminf(fmaxf(ref.y, -(float)a.H), (float)a.H));
+        wx0 = max(tx0 - R - F::STAGE_MARGIN + ox - 1, 0) / E * E;
+        wx1 = (min(tx0 + LK_TW + R + F::STAGE_MARGIN + ox + 3, a.pitch) + E - 1) / E * E;   // pitch: multiple of E
+        wy0 = max(ty0 - R - F::STAGE_MARGIN + oy - 1, 0);
+        wy1 = min(ty0 + LK_TH + R + F::STAGE_MARGIN + oy + 3, a.H);
+        rowbytes = (wx1 - wx0) * (int)sizeof(T);
+        const int rows = wy1 - wy0;
+        staged = wx1 > wx0 && rows > 0 && rows * rowbytes <= F::WIN_BYTES;
+        if (staged) {
+            if (threadIdx.x < 32) {
+                if (threadIdx.x == 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(bar, (uint32_t)(rows * rowbytes));
+                }
+                __syncwarp();
+                fence_proxy_async_global();
+                for (int k = threadIdx.x; k < rows; k += 32)
+                    bulk_g2s(win + k * rowbytes, I2 + (size_t)(wy0 + k) * a.pitch + wx0, (uint32_t)rowbytes, bar);
             }
-            __syncwarp();
-            fence_proxy_async_global();
-            for (int k = threadIdx.x; k < bh; k += 32)
-                bulk_g2s(raw + k * rowbytes, I2 + (size_t)(by0 + k) * a.pitch + (size_t)cx0 * E, (uint32_t)rowbytes, bar);
+            const bool done = mbar_wait_bounded(bar, phase, STAGE_TIMEOUT_NS);
+            phase ^= 1u;
+            if (__syncthreads_or(!done)) {
+                if (threadIdx.x == 0 && a.status) atomicExch(a.status, DEV_TIMEOUT);
+                return false;
+            }
         }
-        const bool done = mbar_wait_bounded(bar, phase, STAGE_TIMEOUT_NS);
-        phase ^= 1u;
-        if (__syncthreads_or(!done)) {
-            if (threadIdx.x == 0 && a.status) atomicExch(a.status, DEV_TIMEOUT);
-            return false;
-        }
-        // convert the box to FP32
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int skip = (bx0 - cx0 * E) * (int)sizeof(T);
-        for (int r = warp; r < bh; r += LK_THREADS / 32) {
-            const unsigned char *src = raw + r * rowbytes + skip;
-            float *dst = fbox + r * bw;
-            for (int c = lane; c < bw; c += 32) dst[c] = ld_smem_elem<T>(src + c * (int)sizeof(T));
-        }
-        __syncthreads();   // the raw copy is consumed before the product planes are written
     }
     // stage 1: products over the tile and its R-pixel halo. The current estimates of
     // S1 pixels are loaded before any of them is used, so that their latencies overlap.
@@ -718,10 +676,9 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
             float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f, p4 = 0.0f;
             if (in[u]) {
                 float Iw, gx, gy;
-                if (staged)
-                    sample_grad_box(fbox, bw, bx0, by0, a.H, a.W, (float)x + f[u].x, (float)y + f[u].y, Iw, gx, gy);
-                else
-                    sample_grad<NC>(I2, a.pitch, a.H, a.W, (float)x + f[u].x, (float)y + f[u].y, Iw, gx, gy);
+                const float px = (float)x + f[u].x, py = (float)y + f[u].y;
+                if (!(staged && sample_grad_win<T>(win, rowbytes, wx0, wy0, wx1, wy1, a.H, a.W, px, py, Iw, gx, gy)))
+                    sample_grad<NC>(I2, a.pitch, a.H, a.W, px, py, Iw, gx, gy);
                 const float e = resid(ldf<NC>(I1 + (y * a.pitch + x)), Iw, gx, gy, f[u].x - ref.x, f[u].y - ref.y);
                 p0 = gx * gx;
                 p1 = gx * gy;
