@@ -167,7 +167,7 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  * batch shape has the same results to within the stated tolerances whichever tuning
  * runs it; with grouped sums (generic_sums == 0) they are the results of of_compute bit
  * for bit. Without a table entry a batch runs {generic_sums 0, stage_i2 0,
- * blocks_per_sm 0, phased 1, prefetch 1}. A tuning:
+ * blocks_per_sm 0, phased 1, prefetch 0}. A tuning:
  *   generic_sums   1: per-output window sums of the run-time-radius kernel;
  *                  0: grouped sums of the kernel specialised for the radius
  *   stage_i2       1: stage I2 footprints in shared memory (specialised kernel only)

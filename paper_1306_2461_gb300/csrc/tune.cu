@@ -134,11 +134,11 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
     const of_plan &p0 = hs[0]->plan;
     // candidates: the grouped fixed-radius sums (gathered or staged I2) when the radius
     // has a specialised kernel, the per-output sums of the run-time-radius kernel; each
-    // as phase launches with an L2 prefetch 1, 0 or 3 blocks per SM ahead, and as the
+    // as phase launches with no L2 prefetch or one 1 or 3 blocks per SM ahead, and as the
     // persistent launch at full occupancy and at 2 and 1 blocks per SM
     std::vector<Tuning> cand;
     const int occ[6] = {-1, -2, -3, 0, 2, 1};   // < 0: phase launches with prefetch pf_of[-1 - b]
-    const int pf_of[3] = {1, 0, 3};
+    const int pf_of[3] = {0, 1, 3};
     for (int gs = radius_is_specialised(p0.radius) ? 0 : 1; gs <= 1; ++gs)
         for (int sg = 0; sg <= (gs ? 0 : 1); ++sg)
             for (int b : occ) {

@@ -316,7 +316,7 @@ def tuning_get(method: Plan, size_class: int) -> dict | None:
     return t.as_dict()
 
 
-def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=0, blocks_per_sm=0, phased=1, prefetch=1):
+def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=0, blocks_per_sm=0, phased=1, prefetch=0):
     """of_tuning_set; the defaults are the library's tuning without a table entry."""
     t = Tuning(int(generic_sums), int(stage_i2), int(blocks_per_sm), int(phased), int(prefetch), 0.0)
     _check(_lib.of_tuning_set(ctypes.byref(method), int(size_class), ctypes.byref(t)), "of_tuning_set")

@@ -109,6 +109,6 @@ def test_tuning_table_host_calls(of):
         of.tuning_set(m, 20, blocks_per_sm=2, phased=1)                   # occupancy is a persistent-launch knob
     of.tuning_set(m, 20)
     t = of.tuning_get(m, 20)
-    assert (t["phased"], t["prefetch"]) == (1, 1)
+    assert (t["phased"], t["prefetch"]) == (1, 0)
     of.tuning_clear()
     assert of.tuning_get(m, 20) is None
