@@ -281,3 +281,33 @@ def test_paper_roi_radius10(of, oracle_mod):
     check(u, v, p, oracle_mod, 4, 10, 2, "f32", "1792x384 u8 r10")
     rms, mx = epe(u, v, p, (10 + 2) * 8)
     print(f"EPE vs ground truth: rms {rms:.4f} max {mx:.4f}")
+
+
+@pytest.mark.parametrize("storage", ["f16", "f32"])
+@pytest.mark.parametrize("H,W,d", [(96, 200, (9.3, -7.6)), (61, 47, (-5.2, 6.7)), (33, 30, (12.4, 3.1)),
+                                   (130, 75, (-11.8, -10.4))])
+def test_staged_window_with_large_displacements(of, storage, H, W, d):
+    # one level, so the whole displacement is estimated at full resolution: the staged
+    # window is displaced by the tile's reference flow, runs partly outside the image or
+    # is larger than it; the fields equal the gathered ones bit for bit (f32 storage is
+    # larger than the window capacity at some radii and falls back to gathering)
+    import torch
+    I1, I2 = synth.translated_texture_pair(H, W, d, seed=H * W, amp=800.0, offset=2000.0, fmax=1.0 / 12.0)
+    I1 = np.rint(I1).astype(np.uint16)
+    I2 = np.rint(I2).astype(np.uint16)
+    for r in (2, 4, 10):
+        g = gpu_flow((I1, I2), 1, r, 6, storage, bits=12)
+        s = gpu_flow((I1, I2), 1, r, 6, storage, bits=12, flags=of.OF_FLAG_STAGE_I2)
+        assert np.array_equal(g[0], s[0]) and np.array_equal(g[1], s[1]), r
+    # and the staged path through the batched phase launches (tuning forced to staging)
+    plan = of.Plan.make(H, W, 2, 4, 4, bits=12, storage=storage)
+    sc = None
+    with of.Flow(plan) as f:
+        sc = of.batch_size_class([f])
+        of.tuning_set(plan, sc, stage_i2=1)
+        ub, vb = of.compute_batch([f], [to_dev(I1)], [to_dev(I2)])
+        torch.cuda.synchronize()
+    of.tuning_clear()
+    ug, vg = gpu_flow((I1, I2), 2, 4, 4, storage, bits=12)
+    assert np.array_equal(ub[0].cpu().numpy().astype(np.float64), ug)
+    assert np.array_equal(vb[0].cpu().numpy().astype(np.float64), vg)
