@@ -63,6 +63,14 @@ def algorithmic_bytes(H, W, L, n, s, raw):
     return pyr + it, pyr, it
 
 
+def algorithmic_bytes_i1grad(H, W, L, n, s, raw):
+    """The same for the first-image-gradient variant: per level the window matrices are
+    written once (16 B/px, after reading I1 at s B/px) and read by every iteration."""
+    tot, pyr, it = algorithmic_bytes(H, W, L, n, s, raw)
+    extra = sum(h * w * (s + 16 + 16 * n) for h, w in level_sizes(H, W, L))
+    return tot + extra, pyr, it + extra
+
+
 def pixel_iterations(H, W, L, n):
     return n * sum(h * w for h, w in level_sizes(H, W, L))
 
@@ -76,10 +84,11 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(kernel_hash):
+def recorded_traffic(kernel_hash, variant=False):
     """DRAM bytes per step (all kernels of one graph replay) from the committed ncu
     summary, if it was taken on this exact kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "batch_step_pair1024_traffic.txt")
+    name = "batch_step_i1grad_pair1024_traffic.txt" if variant else "batch_step_pair1024_traffic.txt"
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     kv = {}
@@ -241,6 +250,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the single-pair and e2e legs")
     ap.add_argument("--no-autotune", action="store_true", help="run the batched launch with the default tuning")
+    ap.add_argument("--i1grad", action="store_true",
+                    help="time the first-image-gradient variant (window matrix fixed per level) as the step")
     ap.add_argument("--table1", action="store_true",
                     help="sweep levels {3,4} x iterations 1..7 at 1792x384, r = 10 (synthetic Table 1) and exit")
     args = ap.parse_args()
@@ -277,7 +288,8 @@ def main():
     I1 = [dev(src[i % DISTINCT].I1) for i in range(B)]
     I2 = [dev(src[i % DISTINCT].I2) for i in range(B)]
     stream = torch.cuda.Stream()
-    plan16 = of.Plan.make(H, W, LEVELS, RADIUS, ITERS, bits=BITS, storage="f16")
+    plan16 = of.Plan.make(H, W, LEVELS, RADIUS, ITERS, bits=BITS, storage="f16",
+                          flags=of.OF_FLAG_I1GRAD if args.i1grad else 0)
     flows = [of.Flow(plan16) for _ in range(B)]
     us = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(B)]
     vs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(B)]
@@ -321,7 +333,7 @@ def main():
     value = fields / (total_ms / 1000.0)
 
     extras = {}
-    if not args.no_extras:
+    if not args.no_extras and not args.i1grad:
         extras = extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows, world)
 
     # accuracy of the timed configuration on one pair (outside the timed region)
@@ -338,17 +350,22 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return 0
-    alg, alg_pyr, alg_it = algorithmic_bytes(H, W, LEVELS, ITERS, 2, 2)
+    alg, alg_pyr, alg_it = (algorithmic_bytes_i1grad if args.i1grad else algorithmic_bytes)(H, W, LEVELS, ITERS, 2, 2)
     phased = tuning["best"]["phased"] if tuning else 1
     groups = (B + 63) // 64
-    launches_per_step = groups * (max(LEVELS - 1, 1) + LEVELS * ITERS) if phased else 1
-    step_kernels = (f"batch step: {groups * max(LEVELS - 1, 1)} phase_pyr_kernel + {groups * LEVELS * ITERS} "
-                    "phase_iter_kernel launches" if phased else "batch step: 1 persistent batch_kernel launch")
+    if args.i1grad:
+        launches_per_step = groups * (max(LEVELS - 1, 1) + LEVELS + LEVELS * ITERS)
+        step_kernels = (f"batch step: {groups * max(LEVELS - 1, 1)} phase_pyr_kernel + {groups * LEVELS} "
+                        f"phase_hess_kernel + {groups * LEVELS * ITERS} phase_i1_iter_kernel launches")
+    else:
+        launches_per_step = groups * (max(LEVELS - 1, 1) + LEVELS * ITERS) if phased else 1
+        step_kernels = (f"batch step: {groups * max(LEVELS - 1, 1)} phase_pyr_kernel + {groups * LEVELS * ITERS} "
+                        "phase_iter_kernel launches" if phased else "batch step: 1 persistent batch_kernel launch")
     peak, peak_kind = measured_peaks()
     launch_ms = statistics.mean(step_ms)
     achieved = alg * B / (launch_ms / 1000.0) / 1e9
     khash = kernel_source_hash()
-    traffic = recorded_traffic(khash)
+    traffic = recorded_traffic(khash, args.i1grad)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -357,6 +374,8 @@ def main():
         "config": {"workload": WORKLOAD, "H": H, "W": W, "bits": BITS, "levels": LEVELS, "radius": RADIUS,
                    "iterations": ITERS, "pairs_per_step": B, "distinct_pairs": DISTINCT,
                    "form": "batched (of_compute_batch), one CUDA graph replay per step",
+                   "method": ("first-image-gradient variant (window matrix fixed per level)" if args.i1grad
+                              else "second-image gradient at the displaced position"),
                    "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased",
                                                                "prefetch")}
                               if tuning else "default (autotuner off)"),
