@@ -495,7 +495,7 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
         of.compute_batch_host(flows, h1, h2, hu, hv, I1, I2, us, vs, stream=stream, chunk=0)
 
     Ke = max(3, args.steps // 2)
-    for key, fn, path in (("e2e", e2e_pipelined, "pinned host frames -> of_compute_batch_host (4 chunks; uploads and "
+    for key, fn, path in (("e2e", e2e_pipelined, "pinned host frames -> of_compute_batch_host (6 chunks; uploads and "
                                                  "downloads on two copy streams overlap the launches) -> pinned host u, v"),
                           ("e2e_unpipelined", e2e_serial, "pinned host frames -> of_compute_batch -> pinned host u, v, "
                                                           "copies and launch in order on one stream")):

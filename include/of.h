@@ -147,7 +147,7 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
 
 /*
  * of_compute_batch from and to HOST buffers, with the copies overlapped with the
- * computation. The pairs are taken in chunks of `chunk` pairs (0: four chunks): chunk
+ * computation. The pairs are taken in chunks of `chunk` pairs (0: six chunks): chunk
  * k's frames are uploaded (hI1s/hI2s -> dI1s/dI2s) on an internal stream, its
  * persistent launch runs on `stream` after that upload, and its fields are downloaded
  * (dus/dvs -> hus/hvs) on a second internal stream after the launch, so the uploads

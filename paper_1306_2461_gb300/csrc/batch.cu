@@ -634,7 +634,7 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
             return OF_EINVAL;
         if (!hI1s[i] && !hs[i]->has_prev) return OF_ESTATE;
     }
-    const int per = chunk > 0 ? chunk : (n + 3) / 4;
+    const int per = chunk > 0 ? chunk : (n + 5) / 6;   // default: six chunks (measured best of 2-8)
     const int nch = (n + per - 1) / per;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     HostPipe pp;

@@ -265,7 +265,7 @@ def _host_ptr(t: torch.Tensor | None, dtype, p: Plan, name: str) -> int | None:
 
 def compute_batch_host(flows, hI1s, hI2s, hus, hvs, dI1s, dI2s, dus, dvs, stream=None, chunk=0):
     """of_compute_batch_host: frames from host tensors, fields into host tensors, the
-    copies overlapped with the batched launches (chunks of `chunk` pairs, 0 = four
+    copies overlapped with the batched launches (chunks of `chunk` pairs, 0 = six
     chunks). hI1s[i] = None reuses the previous pyramid. Synchronise `stream` before
     reading hus/hvs."""
     n = len(flows)
