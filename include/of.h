@@ -134,13 +134,17 @@ int of_create(const of_plan *p, of_handle *out);
 int of_compute(of_handle h, const void *I1, const void *I2, float *u, float *v, of_stream_t stream);
 
 /*
- * Compute n independent fields in one persistent launch (fields are independent,
- * Sect. 3.3, so they can share the GPU). hs[i] are handles whose plans have equal
- * levels, radius, iterations, in_format, in_bits and storage (sizes may differ);
- * a handle may appear at most once. I1s[i] may be NULL (reuse, as in of_compute).
- * All pointers as in of_compute. n == 0 is a no-op. OF_EINVAL on mismatched plans,
- * repeated handles or NULL pointers; OF_ESTATE as in of_compute.
- * The results are those of n separate of_compute calls.
+ * Compute n independent fields together (fields are independent, Sect. 3.3, so they
+ * can share the GPU): one CUDA graph replay per call of either one launch per phase
+ * (pyramid pass, one iteration of one level) over the tiles of up to 64 pairs, or one
+ * persistent cooperative launch with bounded grid barriers between phases, as the
+ * tuning table says (of_autotune_batch below). hs[i] are handles whose plans have
+ * equal levels, radius, iterations, in_format, in_bits, storage and method flags
+ * (sizes may differ); a handle may appear at most once. I1s[i] may be NULL (reuse, as
+ * in of_compute). All pointers as in of_compute. n == 0 is a no-op. OF_EINVAL on
+ * mismatched plans, repeated handles or NULL pointers; OF_ESTATE as in of_compute.
+ * The results are those of n separate of_compute calls (bit for bit with the grouped
+ * window sums, the default).
  */
 int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
                      float *const *us, float *const *vs, of_stream_t stream);
@@ -149,7 +153,7 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
  * of_compute_batch from and to HOST buffers, with the copies overlapped with the
  * computation. The pairs are taken in chunks of `chunk` pairs (0: six chunks): chunk
  * k's frames are uploaded (hI1s/hI2s -> dI1s/dI2s) on an internal stream, its
- * persistent launch runs on `stream` after that upload, and its fields are downloaded
+ * batched launch runs on `stream` after that upload, and its fields are downloaded
  * (dus/dvs -> hus/hvs) on a second internal stream after the launch, so the uploads
  * and downloads of neighbouring chunks overlap the launches. hI1s[i] == NULL reuses
  * the previous pyramid (dI1s[i] is then ignored). Host buffers should be pinned (page-
@@ -285,7 +289,7 @@ int of_debug_wait_timeout(int32_t timeout_us);
  * device and is reused as the first image of the next pair (computing scheme 1 of
  * Sect. 2.4), so each field processes one new image. Streams are admitted against an
  * HBM budget. A worker thread packs the next pending frame of every stream into one
- * persistent batched launch ("tick"); frames arriving while ticks run join the next
+ * batched launch ("tick", tuned as of_compute_batch); frames arriving while ticks run join the next
  * tick as soon as fewer than max_inflight ticks are on the device, their host-to-
  * device copies overlapping the running tick. All calls are thread-safe.
  */

@@ -7,7 +7,7 @@
 // (their workspace plus two staging buffers).
 //
 // A worker thread forms "ticks": the next pending frame of every stream that has one
-// (at most max_batch pairs) goes into one persistent batched launch. Frames that
+// (at most max_batch pairs) goes into one batched launch (tuned as of_compute_batch). Frames that
 // arrive while ticks run join the next tick as soon as fewer than max_inflight ticks
 // are on the device; their host-to-device copies run on a copy stream and overlap the
 // running tick's compute, and the next tick's kernel follows the previous one on the
