@@ -89,6 +89,7 @@ def _load():
         "of_field_minmax": (ctypes.c_int, [vp, i32, i32, vp, vp]),
         "of_debug_fail_allocs": (ctypes.c_int, [i32]),
         "of_compute_batch_host": (ctypes.c_int, [i32, pp, pp, pp, pp, pp, pp, pp, pp, pp, vp, i32]),
+        "of_compute_noalloc": (ctypes.c_int, [P, vp, vp, vp, vp, vp]),
         "of_autotune_batch": (ctypes.c_int, [i32, pp, pp, pp, pp, pp, vp, i32, ctypes.POINTER(Tuning),
                                              ctypes.POINTER(Tuning), i32, ctypes.POINTER(i32)]),
         "of_batch_size_class": (ctypes.c_int, [i32, pp, ctypes.POINTER(i32)]),
@@ -324,6 +325,16 @@ def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=0, blocks
 
 def tuning_clear():
     _check(_lib.of_tuning_clear(), "of_tuning_clear")
+
+
+def compute_noalloc(plan: Plan, I1: torch.Tensor, I2: torch.Tensor, u: torch.Tensor, v: torch.Tensor,
+                    stream=None):
+    """of_compute_noalloc: one pair with no handle and no device allocation (a static
+    32 MiB device scratch shared by all calls; overlapping calls race). Fills u, v."""
+    _check(_lib.of_compute_noalloc(ctypes.byref(plan), _img_ptr(I1, plan, "I1"), _img_ptr(I2, plan, "I2"),
+                                   _flow_ptr(u, plan, "u"), _flow_ptr(v, plan, "v"), _stream(stream)),
+           "of_compute_noalloc")
+    return u, v
 
 
 def window_sums(ch: torch.Tensor, r: int, stream=None) -> torch.Tensor:

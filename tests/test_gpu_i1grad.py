@@ -1,8 +1,6 @@
 """The variant linearised with the first image's gradient (OF_FLAG_I1GRAD): the window
 matrix is summed once per level from I1, each iteration sums two channels. Parity with
 the oracle's variant on the same inputs, to the same tolerances as the main path."""
-import ctypes
-
 import numpy as np
 import pytest
 
@@ -108,12 +106,7 @@ def test_noalloc_entry_accepts_the_variant(of):
     plan = of.Plan.make(128, 160, 2, 4, 3, bits=8, storage="f32", flags=of.OF_FLAG_I1GRAD)
     u = torch.empty(128, 160, device="cuda")
     v = torch.empty(128, 160, device="cuda")
-    fn = of.lib().of_compute_noalloc
-    fn.restype = ctypes.c_int
-    fn.argtypes = [ctypes.POINTER(of.Plan)] + [ctypes.c_void_p] * 5
-    I1, I2 = to_dev(p.I1), to_dev(p.I2)
-    st = torch.cuda.current_stream().cuda_stream
-    assert fn(ctypes.byref(plan), I1.data_ptr(), I2.data_ptr(), u.data_ptr(), v.data_ptr(), st) == of.OF_OK
+    of.compute_noalloc(plan, to_dev(p.I1), to_dev(p.I2), u, v)
     torch.cuda.synchronize()
     ua, va = run(of, p, 2, 4, 3, "f32", bits=8)
     assert np.array_equal(u.cpu().numpy().astype(np.float64), ua)
