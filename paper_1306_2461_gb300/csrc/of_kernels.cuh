@@ -127,11 +127,28 @@ __device__ __forceinline__ void pyr_tile_smem(const PyrArgs &a, int tile, int im
     __syncthreads();
     if (FIRST) {
         Tin *d0 = static_cast<Tin *>(img ? a.dst0[1] : a.dst0[0]);
-        for (int i = threadIdx.x; i < 4 * PYR_TH * PYR_TW; i += blockDim.x) {
-            const int r = i / (2 * PYR_TW), c = i - r * (2 * PYR_TW);
-            const int y = 2 * ty0 + r, x = 2 * tx0 + c;
-            if (y < a.H && x < a.W)
-                d0[(size_t)y * a.dst0_pitch + x] = to_elem<Tin>(s_in[(r + 2) * PYR_RW + c + 2]);
+        // the tile's level-0 pixels, as they are: 16-byte chunks straight from the camera
+        // image when its rows allow it and the tile lies inside the image, else element
+        // by element from shared memory (the same values either way)
+        constexpr int E = 16 / (int)sizeof(Tin);
+        constexpr int CPR = 2 * PYR_TW / E;   // chunks per tile row
+        const bool chunks = 2 * tx0 + 2 * PYR_TW <= a.W && 2 * ty0 + 2 * PYR_TH <= a.H &&
+                            (a.src_pitch * (int)sizeof(Tin)) % 16 == 0 && (a.dst0_pitch * (int)sizeof(Tin)) % 16 == 0 &&
+                            (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(d0) & 15) == 0;
+        if (chunks) {
+            for (int i = threadIdx.x; i < 2 * PYR_TH * CPR; i += blockDim.x) {
+                const int r = i / CPR, c = i - r * CPR;
+                const int y = 2 * ty0 + r, x = 2 * tx0 + c * E;
+                *reinterpret_cast<uint4 *>(d0 + (size_t)y * a.dst0_pitch + x) =
+                    ld<NC>(reinterpret_cast<const uint4 *>(src + (size_t)y * a.src_pitch + x));
+            }
+        } else {
+            for (int i = threadIdx.x; i < 4 * PYR_TH * PYR_TW; i += blockDim.x) {
+                const int r = i / (2 * PYR_TW), c = i - r * (2 * PYR_TW);
+                const int y = 2 * ty0 + r, x = 2 * tx0 + c;
+                if (y < a.H && x < a.W)
+                    d0[(size_t)y * a.dst0_pitch + x] = to_elem<Tin>(s_in[(r + 2) * PYR_RW + c + 2]);
+            }
         }
     }
     Tout *d = static_cast<Tout *>(img ? a.dst[1] : a.dst[0]);
