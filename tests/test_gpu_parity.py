@@ -311,3 +311,24 @@ def test_staged_window_with_large_displacements(of, storage, H, W, d):
     ug, vg = gpu_flow((I1, I2), 2, 4, 4, storage, bits=12)
     assert np.array_equal(ub[0].cpu().numpy().astype(np.float64), ug)
     assert np.array_equal(vb[0].cpu().numpy().astype(np.float64), vg)
+
+
+@pytest.mark.parametrize("H,W", [(16384, 16384), (8192, 32768)])
+def test_maximum_size_identical_images_exactly_zero(of, H, W):
+    # the largest plans (H * W = 2^28, W at its limit): identical images give exactly
+    # zero flow everywhere, per pair and batched (noise images drawn on the device)
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(H + W)
+    I = torch.randint(0, 256, (H, W), dtype=torch.uint8, device="cuda", generator=g)
+    plan = of.Plan.make(H, W, 3, 4, 2, bits=8, storage="f16")
+    with of.Flow(plan) as f:
+        u, v = f.compute(I, I)
+        torch.cuda.synchronize()
+        assert f.sync_status() == of.OF_OK
+        assert int(torch.count_nonzero(u)) == 0 and int(torch.count_nonzero(v)) == 0
+        del u, v
+        ub, vb = of.compute_batch([f], [I], [I])
+        torch.cuda.synchronize()
+        assert int(torch.count_nonzero(ub[0])) == 0 and int(torch.count_nonzero(vb[0])) == 0
+    del I, ub, vb
+    torch.cuda.empty_cache()
