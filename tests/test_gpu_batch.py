@@ -141,6 +141,34 @@ def test_batch_rejects_mixed_methods_and_repeats(of):
     assert ei.value.status == of.OF_ESTATE
 
 
+def test_empty_and_degenerate_batches(of, oracle_mod):
+    import torch
+    # n = 0: a no-op in both batched forms; the autotuner needs at least one pair
+    assert of.compute_batch([], [], []) == ([], [])
+    of.compute_batch_host([], [], [], [], [], [], [], [], [])
+    with pytest.raises(of.OfError) as ei:
+        of.autotune_batch([], [], [], [], [])
+    assert ei.value.status == of.OF_EINVAL
+    # 1x1, 1xW and Hx1 images (every level 1x1 or a single row/column) batched with a
+    # normal pair: the fields equal one of_compute per pair, and the oracle's
+    shapes = [(1, 1), (1, 37), (29, 1), (64, 96)]
+    rng = np.random.default_rng(8)
+    imgs = [(rng.integers(0, 4096, s_).astype(np.uint16), rng.integers(0, 4096, s_).astype(np.uint16))
+            for s_ in shapes]
+    plans = [of.Plan.make(*s_, 3, 2, 3, bits=12, storage="f32") for s_ in shapes]
+    flows = [of.Flow(p_) for p_ in plans]
+    ub, vb = of.compute_batch(flows, [to_dev(a) for a, _ in imgs], [to_dev(b) for _, b in imgs])
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(imgs):
+        u1, v1 = single(of, plans[k], to_dev(a), to_dev(b))
+        assert torch.equal(ub[k], u1) and torch.equal(vb[k], v1), shapes[k]
+        if shapes[k][0] * shapes[k][1] < 64:
+            uo, vo = oracle_mod.flow(a.astype(np.float64), b.astype(np.float64), 3, 2, 3)
+            assert np.abs(ub[k].cpu().numpy() - uo).max() <= 1e-3 and np.abs(vb[k].cpu().numpy() - vo).max() <= 1e-3
+    for f in flows:
+        f.close()
+
+
 @pytest.mark.parametrize("chunk", [0, 1, 3, 64])
 def test_host_buffer_pipeline_equals_device_batch(of, chunk):
     # frames from pinned host memory, fields back to pinned host memory, copies
