@@ -383,13 +383,13 @@ def main():
                    "method": ("first-image-gradient variant (window matrix fixed per level)" if args.i1grad
                               else "second-image gradient at the displaced position"),
                    "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased",
-                                                               "prefetch")}
+                                                               "prefetch", "tile_h")}
                               if tuning else "default (autotuner off)"),
                    "l2": "no flush: per-step working set ~%.1f GB >> 129 MB L2" % (
                        B * (of.workspace_bytes(plan16) + 4 * H * W) / 1e9),
                    "parallelism": f"replicas x{world}"},
         "autotune_candidates_ms": ([[c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"], c["prefetch"],
-                                     round(c["ms"], 3)]
+                                     c["tile_h"], round(c["ms"], 3)]
                                     for c in tuning["candidates"]] if tuning else None),
         "latency_ms": {"step_p50": percentile(step_ms, 50), "step_p99": percentile(step_ms, 99),
                        "step_max": max(step_ms)},

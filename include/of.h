@@ -170,8 +170,8 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  * Autotuning of the batched launch (of_compute_batch and the serving loop). Every
  * batch shape has the same results to within the stated tolerances whichever tuning
  * runs it; with grouped sums (generic_sums == 0) they are the results of of_compute bit
- * for bit. Without a table entry a batch runs {generic_sums 0, stage_i2 0,
- * blocks_per_sm 0, phased 1, prefetch 0}. A tuning:
+ * for bit (with the default tile height). Without a table entry a batch runs
+ * {generic_sums 0, stage_i2 0, blocks_per_sm 0, phased 1, prefetch 0, tile_h 20}. A tuning:
  *   generic_sums   1: per-output window sums of the run-time-radius kernel;
  *                  0: grouped sums of the kernel specialised for the radius
  *   stage_i2       1: stage I2 footprints in shared memory (specialised kernel only)
@@ -182,6 +182,10 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  *                  blocks_per_sm must be 0)
  *   prefetch       phase launches: each iteration block warms L2 with the rows the block
  *                  prefetch x (number of SMs) tiles later will read first (0: off, <= 16)
+ *   tile_h         phase launches with grouped sums: height of the 64-wide iteration tile,
+ *                  20 (the default; 0 means the default) or 32. Tiles other than the
+ *                  default move each tile's reference flow, so their fields differ from
+ *                  of_compute's by rounding (within the stated tolerances)
  *   ms             measured milliseconds per batch (of_autotune_batch output only)
  * The process-wide table is keyed by the method (in_format, storage, radius, levels,
  * iterations, OF_FLAG_ZNSSD) and a size class, round(log2(mean level-0 pixels per pair)).
@@ -192,6 +196,7 @@ typedef struct of_tuning {
     int32_t blocks_per_sm;
     int32_t phased;
     int32_t prefetch;
+    int32_t tile_h;
     float ms;
 } of_tuning;
 

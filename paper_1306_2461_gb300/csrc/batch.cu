@@ -252,6 +252,8 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int32_t prefetch_ahead = sms * t.prefetch;
+    // iteration tile height: the tuned one for the grouped sums of a specialised radius
+    const int tile_h = (t.tile_h == ALT_TH && !t.generic_sums && radius_specialised(p0.radius)) ? ALT_TH : LK_TH;
     cudaError_t e;
     for (int g0 = 0; g0 < n; g0 += PHASE_PAIRS) {
         const int m = n - g0 < PHASE_PAIRS ? n - g0 : PHASE_PAIRS;
@@ -361,7 +363,7 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
                     a.fout_pitch = bp[i].pitch[l];
                 }
                 a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
-                const int th = i1grad ? I1_TH : LK_TH;   // the variant's kernels have their own tile height
+                const int th = i1grad ? I1_TH : tile_h;   // the variant's kernels have their own tile height
                 a.tiles = a.tiles_x * ((a.H + th - 1) / th);
                 a.status = bp[i].status;
                 a.stage_i2 = i1grad ? 0 : stage;
@@ -370,7 +372,8 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
                 I.prefix[i + 1] = I.prefix[i] + a.tiles;
             }
             e = i1grad ? launch_phase_i1_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, st)
-                       : launch_phase_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, st);
+                       : launch_phase_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, tile_h,
+                                           st);
             if (e != cudaSuccess) return e;
         }
     }
@@ -385,6 +388,7 @@ static Tuning effective(const of_plan &p0, Tuning t)
         t.phased = 1;
         t.blocks_per_sm = 0;
         t.stage_i2 = 0;
+        t.tile_h = 0;
     }
     return t;
 }
@@ -506,7 +510,7 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
         const int extra[6] = {p0.radius,
                               (int)(p0.iterations * 16 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD))),
                               hs[0]->device, t.generic_sums, t.stage_i2,
-                              t.blocks_per_sm + 256 * t.phased + 65536 * t.prefetch};
+                              t.blocks_per_sm + 256 * t.phased + 65536 * t.prefetch + (1 << 24) * (t.tile_h != 0)};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
 

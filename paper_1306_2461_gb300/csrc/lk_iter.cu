@@ -46,13 +46,14 @@ cudaError_t launch_i1_iter(const IterArgs &a, int elem, int radius, float fp64_c
 }
 
 #define OF_CASE_PH(R) \
-    case R: return phase_launch<R>(P, elem, radius, fp64_cond, s);
-cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond, cudaStream_t s)
+    case R: return phase_launch<R>(P, elem, radius, fp64_cond, tile_h, s);
+cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond, int tile_h,
+                              cudaStream_t s)
 {
-    if (generic) return phase_launch<0>(P, elem, radius, fp64_cond, s);
+    if (generic) return phase_launch<0>(P, elem, radius, fp64_cond, LK_TH, s);
     switch (radius) {
         OF_RADII(OF_CASE_PH)
-    default: return phase_launch<0>(P, elem, radius, fp64_cond, s);
+    default: return phase_launch<0>(P, elem, radius, fp64_cond, LK_TH, s);
     }
 }
 

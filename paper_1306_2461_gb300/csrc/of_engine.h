@@ -77,6 +77,7 @@ struct Tuning {
     int blocks_per_sm = 0;   // resident blocks per SM of the persistent launch; 0 = as many as fit
     int phased = 1;          // 1: one ordinary launch per phase; 0: the persistent launch with grid barriers
     int prefetch = 0;        // phase launches: warm L2 for the tile this many blocks per SM ahead (0: off)
+    int tile_h = 0;          // phase launches with grouped sums: iteration tile height (0: the default)
 };
 // The tuning table entry for this method and size class, or the default.
 Tuning tuning_for(const of_plan &method, int size_class);

@@ -144,6 +144,12 @@ constexpr int LK_TW = 64;    // iteration output tile width
 #endif
 constexpr int LK_TH = OF_LK_TH;
 static_assert(LK_TH % 4 == 0, "the vertical box pass takes 4 rows at a time");
+// The other iteration tile height the tuning can choose for the phase launches (64 x ALT_TH).
+#ifndef OF_ALT_TH
+#define OF_ALT_TH 32
+#endif
+constexpr int ALT_TH = OF_ALT_TH;
+static_assert(ALT_TH % 4 == 0 && ALT_TH != LK_TH, "a multiple of 4 other than LK_TH");
 // Output tile height of the first-image-gradient variant's kernels (two product planes,
 // so a taller tile still leaves room for many blocks per SM).
 #ifndef OF_I1_TH
@@ -167,6 +173,14 @@ constexpr int MAX_RADIUS = OF_MAX_RADIUS;
 // paper's radii); any other radius runs the generic kernel.
 #define OF_RADII(X) X(2) X(3) X(4) X(5) X(6) X(8) X(10)
 
+inline bool radius_specialised(int r)
+{
+#define OF_IS_RADIUS(R) if (r == R) return true;
+    OF_RADII(OF_IS_RADIUS)
+#undef OF_IS_RADIUS
+    return false;
+}
+
 // ------------------------------------------------------------------- launchers
 // All return cudaGetLastError() of their launch.
 cudaError_t launch_pyr_first(const PyrArgs &a, int in_format, int storage, cudaStream_t s);
@@ -181,7 +195,8 @@ cudaError_t launch_i1_iter(const IterArgs &a, int elem, int radius, float fp64_c
 // Phase launches of the batched method (grid = P.prefix[P.npairs] blocks).
 cudaError_t launch_phase_pyr(const PyrPhase &P, bool first, int in_format, int storage, cudaStream_t s);
 cudaError_t launch_phase_zn(const ZnPhase &P, int in_format, int storage, cudaStream_t s);
-cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond, cudaStream_t s);
+cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond, int tile_h,
+                              cudaStream_t s);
 // The first-image-gradient variant: window matrices of one level, then its iterations.
 cudaError_t launch_phase_hess(const HessPhase &P, int elem, int radius, bool generic, cudaStream_t s);
 cudaError_t launch_phase_i1_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond,
@@ -198,7 +213,7 @@ cudaError_t configure_lk_kernels();   // all kernels with dynamic shared memory,
 template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
 template <int R> cudaError_t i1h_launch(const HessArgs &a, int elem, int r, cudaStream_t s);
-template <int R> cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, cudaStream_t s);
+template <int R> cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, int tile_h, cudaStream_t s);
 template <int R> cudaError_t phase_hess_launch(const HessPhase &P, int elem, int r, cudaStream_t s);
 template <int R> cudaError_t phase_i1_launch(const IterPhase &P, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> cudaError_t i1_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);

@@ -492,7 +492,11 @@ template <int R, int TH = LK_TH> struct FixedTile {
 #ifndef OF_LK_MIN_BLOCKS
 #define OF_LK_MIN_BLOCKS 5   // resident blocks per SM the fixed-radius kernels are compiled for (R <= 6)
 #endif
-    static constexpr int MIN_BLOCKS = R <= 6 ? OF_LK_MIN_BLOCKS : 2;
+    // resident blocks per SM the kernels are compiled for: the measured choice for the
+    // default tile height, else as many as the shared memory holds (at most 5)
+    static constexpr int SMEM_FIT = 233472 / (4 * (5 * PLANE + 4) + 1024);
+    static constexpr int MIN_BLOCKS =
+        TH == LK_TH ? (R <= 6 ? OF_LK_MIN_BLOCKS : 2) : (SMEM_FIT < 1 ? 1 : (SMEM_FIT > 5 ? 5 : SMEM_FIT));
 };
 
 constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's row copies
@@ -609,10 +613,10 @@ __device__ __forceinline__ void box_v4(const float *P, int g, int tx, float s[C]
 }
 
 // The tile's mbarrier: initialised once per block, before the first tile.
-template <int R> __device__ __forceinline__ void lk_tile_init(float *smem)
+template <int R, int TH = LK_TH> __device__ __forceinline__ void lk_tile_init(float *smem)
 {
     if (threadIdx.x == 0) {
-        mbar_init(reinterpret_cast<uint64_t *>(smem + FixedTile<R>::OFF_BAR), 1);
+        mbar_init(reinterpret_cast<uint64_t *>(smem + FixedTile<R, TH>::OFF_BAR), 1);
         fence_proxy_async_smem();
     }
     __syncthreads();
@@ -620,17 +624,17 @@ template <int R> __device__ __forceinline__ void lk_tile_init(float *smem)
 
 // Returns false if the staging copy did not complete in time (then OF_ETIMEOUT is in
 // *a.status, nothing of the tile was written, and the block must stop).
-template <typename T, bool NC, int R, int MODE>
+template <typename T, bool NC, int R, int MODE, int TH = LK_TH>
 __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float fp64_cond, float *smem,
                                               uint32_t &phase)
 {
-    using F = FixedTile<R>;
+    using F = FixedTile<R, TH>;
     float *P = smem;
     unsigned char *win = reinterpret_cast<unsigned char *>(smem + F::OFF_WIN);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + F::OFF_BAR);
     const int tyi = tile / a.tiles_x;
-    const int ty0 = tyi * LK_TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
-    const float2 ref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + LK_TH / 2, a.H - 1));
+    const int ty0 = tyi * TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
+    const float2 ref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + TH / 2, a.H - 1));
     const T *I1 = static_cast<const T *>(a.I1);
     const T *I2 = static_cast<const T *>(a.I2);
     __syncthreads();   // the previous tile's readers of smem are done
@@ -646,7 +650,7 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
         wx0 = max(tx0 - R - F::STAGE_MARGIN + ox - 1, 0) / E * E;
         wx1 = (min(tx0 + LK_TW + R + F::STAGE_MARGIN + ox + 3, a.pitch) + E - 1) / E * E;   // pitch: multiple of E
         wy0 = max(ty0 - R - F::STAGE_MARGIN + oy - 1, 0);
-        wy1 = min(ty0 + LK_TH + R + F::STAGE_MARGIN + oy + 3, a.H);
+        wy1 = min(ty0 + TH + R + F::STAGE_MARGIN + oy + 3, a.H);
         rowbytes = (wx1 - wx0) * (int)sizeof(T);
         const int rows = wy1 - wy0;
         staged = wx1 > wx0 && rows > 0 && rows * rowbytes <= F::WIN_BYTES;
@@ -712,16 +716,16 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
         }
     }
     __syncthreads();
-    box_h_inplace<R>(P);
+    box_h_inplace<R, 5, TH>(P);
     // vertical sums, solve and write, 4 rows of one column per item
-    constexpr int VITEMS = LK_TW * (LK_TH / 4);
+    constexpr int VITEMS = LK_TW * (TH / 4);
 #pragma unroll 1
     for (int i = threadIdx.x; i < VITEMS; i += LK_THREADS) {
         const int tx = i % LK_TW, g = i / LK_TW;
         const int x = tx0 + tx;
         if (x >= a.W || ty0 + 4 * g >= a.H) continue;
         float s[5][4];
-        box_v4<R>(P, g, tx, s);
+        box_v4<R, 5, TH>(P, g, tx, s);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int y = ty0 + 4 * g + j;
@@ -743,7 +747,7 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
 // The iteration tile for radius R (0 = generic, radius r at run time). MODE: the flow
 // mode when it is known at compile time (-1: read a.mode at run time). Returns false
 // when the block must stop (a staging copy timed out; recorded in *a.status).
-template <typename T, bool NC, int R, int MODE = -1>
+template <typename T, bool NC, int R, int MODE = -1, int TH = LK_TH>
 __device__ __forceinline__ bool lk_tile(const IterArgs &a, int tile, int r, float fp64_cond, float *smem,
                                         uint32_t &phase)
 {
@@ -751,19 +755,19 @@ __device__ __forceinline__ bool lk_tile(const IterArgs &a, int tile, int r, floa
         lk_tile_generic<T, NC>(a, tile, r, fp64_cond, smem);
         return true;
     } else {
-        return lk_tile_fixed<T, NC, R, MODE>(a, tile, fp64_cond, smem, phase);
+        return lk_tile_fixed<T, NC, R, MODE, TH>(a, tile, fp64_cond, smem, phase);
     }
 }
 
-template <int R> __device__ __forceinline__ void lk_tile_prepare(float *smem)
+template <int R, int TH = LK_TH> __device__ __forceinline__ void lk_tile_prepare(float *smem)
 {
-    if constexpr (R != 0) lk_tile_init<R>(smem);
+    if constexpr (R != 0) lk_tile_init<R, TH>(smem);
 }
 
-template <int R> constexpr int lk_min_blocks()
+template <int R, int TH = LK_TH> constexpr int lk_min_blocks()
 {
     if constexpr (R == 0) return 2;
-    else return FixedTile<R>::MIN_BLOCKS;
+    else return FixedTile<R, TH>::MIN_BLOCKS;
 }
 
 #ifndef OF_BATCH_MIN_BLOCKS
@@ -776,10 +780,10 @@ template <int R> constexpr int batch_min_blocks()
     return m < OF_BATCH_MIN_BLOCKS ? m : OF_BATCH_MIN_BLOCKS;
 }
 
-template <int R> inline __host__ __device__ int lk_tile_smem_floats(int r, bool stage_i2)
+template <int R, int TH = LK_TH> inline __host__ __device__ int lk_tile_smem_floats(int r, bool stage_i2)
 {
     if constexpr (R == 0) return lk_smem_floats(r);
-    else return stage_i2 ? FixedTile<R>::SMEM_FLOATS : FixedTile<R>::SMEM_NOSTAGE;
+    else return stage_i2 ? FixedTile<R, TH>::SMEM_FLOATS : FixedTile<R, TH>::SMEM_NOSTAGE;
 }
 
 }  // namespace of

@@ -25,8 +25,8 @@ __global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>()) lk_iter_kernel
 
 // One iteration of up to PHASE_PAIRS pairs on one level: block b runs tile
 // b - prefix[p] of pair p. The same tile code as lk_iter_kernel, so the same results.
-template <typename T, int R, int MODE>
-__global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>())
+template <typename T, int R, int MODE, int TH>
+__global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R, TH>())
 phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
 {
     extern __shared__ float4 smem4[];
@@ -35,13 +35,13 @@ phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
         const int t2 = blockIdx.x + P.ahead;
         if (P.ahead > 0 && t2 < P.prefix[P.npairs]) {
             const int q = phase_pair(P.prefix, P.npairs, t2);
-            prefetch_tile<T, MODE>(P.a[q], t2 - P.prefix[q], R);
+            prefetch_tile<T, MODE, TH>(P.a[q], t2 - P.prefix[q], R);
         }
     }
     const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
     uint32_t phase = 0;
-    lk_tile_prepare<R>(smem);
-    lk_tile<T, true, R, MODE>(P.a[p], blockIdx.x - P.prefix[p], r, fp64_cond, smem, phase);
+    lk_tile_prepare<R, TH>(smem);
+    lk_tile<T, true, R, MODE, TH>(P.a[p], blockIdx.x - P.prefix[p], r, fp64_cond, smem, phase);
 }
 
 // The window sums of five given planes, through the same passes as the iteration tile.
@@ -136,30 +136,41 @@ template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, flo
     return cudaGetLastError();
 }
 
-// The flow mode is the same for every pair of a phase: one kernel per mode.
-template <typename T, int R>
-static cudaError_t phase_for(const IterPhase &P, int r, float fp64_cond, cudaStream_t s)
+// The flow mode is the same for every pair of a phase: one kernel per mode (and per
+// tile height; the run-time-radius kernel has only the default height).
+template <typename T, int R, int TH>
+static cudaError_t phase_for_th(const IterPhase &P, int r, float fp64_cond, cudaStream_t s)
 {
     const bool stage = P.a[0].stage_i2 != 0;
-    const size_t smem = sizeof(float) * lk_tile_smem_floats<R>(r, stage);
+    const size_t smem = sizeof(float) * lk_tile_smem_floats<R, TH>(r, stage);
     const int blocks = P.prefix[P.npairs];
     switch (P.a[0].mode) {
-    case FLOW_ZERO: phase_iter_kernel<T, R, FLOW_ZERO><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
-    case FLOW_SAME: phase_iter_kernel<T, R, FLOW_SAME><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
-    default: phase_iter_kernel<T, R, FLOW_UPSAMPLE><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
+    case FLOW_ZERO: phase_iter_kernel<T, R, FLOW_ZERO, TH><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
+    case FLOW_SAME: phase_iter_kernel<T, R, FLOW_SAME, TH><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
+    default: phase_iter_kernel<T, R, FLOW_UPSAMPLE, TH><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
     }
     return cudaGetLastError();
 }
 
-template <int R> cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, cudaStream_t s)
+template <typename T, int R>
+static cudaError_t phase_for(const IterPhase &P, int r, float fp64_cond, int tile_h, cudaStream_t s)
+{
+    if constexpr (R != 0) {
+        if (tile_h == ALT_TH) return phase_for_th<T, R, ALT_TH>(P, r, fp64_cond, s);
+    }
+    return phase_for_th<T, R, LK_TH>(P, r, fp64_cond, s);
+}
+
+template <int R>
+cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, int tile_h, cudaStream_t s)
 {
     if (P.prefix[P.npairs] == 0) return cudaSuccess;
     switch (elem) {
-    case ET_U8: return phase_for<uint8_t, R>(P, r, fp64_cond, s);
-    case ET_U16: return phase_for<uint16_t, R>(P, r, fp64_cond, s);
-    case ET_F32: return phase_for<float, R>(P, r, fp64_cond, s);
-    case ET_F16: return phase_for<__half, R>(P, r, fp64_cond, s);
-    default: return phase_for<__nv_bfloat16, R>(P, r, fp64_cond, s);
+    case ET_U8: return phase_for<uint8_t, R>(P, r, fp64_cond, tile_h, s);
+    case ET_U16: return phase_for<uint16_t, R>(P, r, fp64_cond, tile_h, s);
+    case ET_F32: return phase_for<float, R>(P, r, fp64_cond, tile_h, s);
+    case ET_F16: return phase_for<__half, R>(P, r, fp64_cond, tile_h, s);
+    default: return phase_for<__nv_bfloat16, R>(P, r, fp64_cond, tile_h, s);
     }
 }
 
@@ -258,14 +269,29 @@ template <int R> cudaError_t radius_configure()
     OF_SET((lk_iter_kernel<float, R>));
     OF_SET((lk_iter_kernel<__half, R>));
     OF_SET((lk_iter_kernel<__nv_bfloat16, R>));
-#define OF_SET_PH(T) OF_SET((phase_iter_kernel<T, R, FLOW_ZERO>)); OF_SET((phase_iter_kernel<T, R, FLOW_SAME>)); \
-    OF_SET((phase_iter_kernel<T, R, FLOW_UPSAMPLE>))
+#define OF_SET_PH(T) OF_SET((phase_iter_kernel<T, R, FLOW_ZERO, LK_TH>)); OF_SET((phase_iter_kernel<T, R, FLOW_SAME, LK_TH>)); \
+    OF_SET((phase_iter_kernel<T, R, FLOW_UPSAMPLE, LK_TH>))
     OF_SET_PH(uint8_t);
     OF_SET_PH(uint16_t);
     OF_SET_PH(float);
     OF_SET_PH(__half);
     OF_SET_PH(__nv_bfloat16);
 #undef OF_SET_PH
+    if constexpr (R != 0) {   // the other tile height of the phase kernels
+        const int alt = (int)sizeof(float) * lk_tile_smem_floats<R, ALT_TH>(R, true);
+#define OF_SET_ALT(T)                                                                                       \
+    for (const void *fn : {(const void *)phase_iter_kernel<T, R, FLOW_ZERO, ALT_TH>,                        \
+                           (const void *)phase_iter_kernel<T, R, FLOW_SAME, ALT_TH>,                        \
+                           (const void *)phase_iter_kernel<T, R, FLOW_UPSAMPLE, ALT_TH>})                   \
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, alt)) != cudaSuccess) \
+            return e;
+        OF_SET_ALT(uint8_t)
+        OF_SET_ALT(uint16_t)
+        OF_SET_ALT(float)
+        OF_SET_ALT(__half)
+        OF_SET_ALT(__nv_bfloat16)
+#undef OF_SET_ALT
+    }
     OF_SET((window_sums_kernel<R>));
     {
         const int r = R == 0 ? MAX_RADIUS : R;
@@ -296,7 +322,7 @@ template <int R> cudaError_t radius_configure()
 template cudaError_t lk_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template cudaError_t ws_launch<OF_RADIUS>(const float *, int, int, int, float *, cudaStream_t);
 template cudaError_t i1h_launch<OF_RADIUS>(const HessArgs &, int, int, cudaStream_t);
-template cudaError_t phase_launch<OF_RADIUS>(const IterPhase &, int, int, float, cudaStream_t);
+template cudaError_t phase_launch<OF_RADIUS>(const IterPhase &, int, int, float, int, cudaStream_t);
 template cudaError_t phase_hess_launch<OF_RADIUS>(const HessPhase &, int, int, cudaStream_t);
 template cudaError_t phase_i1_launch<OF_RADIUS>(const IterPhase &, int, int, float, cudaStream_t);
 template cudaError_t i1_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);

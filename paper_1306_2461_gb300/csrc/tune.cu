@@ -29,19 +29,12 @@ Key key_of(const of_plan &m, int size_class)
     return {m.in_format, m.storage, m.radius, m.levels, m.iterations, (m.flags & OF_FLAG_ZNSSD) ? 1 : 0, size_class};
 }
 
-bool radius_is_specialised(int r)
-{
-#define OF_IS(R) if (r == R) return true;
-    OF_RADII(OF_IS)
-#undef OF_IS
-    return false;
-}
-
 bool valid(const Tuning &t)
 {
     return t.generic_sums >= 0 && t.generic_sums <= 1 && t.stage_i2 >= 0 && t.stage_i2 <= 1 && t.blocks_per_sm >= 0 &&
            t.blocks_per_sm <= 64 && t.phased >= 0 && t.phased <= 1 && !(t.generic_sums && t.stage_i2) &&
-           !(t.phased && t.blocks_per_sm) && t.prefetch >= 0 && t.prefetch <= 16;
+           !(t.phased && t.blocks_per_sm) && t.prefetch >= 0 && t.prefetch <= 16 &&
+           (t.tile_h == 0 || t.tile_h == LK_TH || (t.tile_h == ALT_TH && t.phased && !t.generic_sums));
 }
 
 void to_c(const Tuning &t, float ms, of_tuning *o)
@@ -51,6 +44,7 @@ void to_c(const Tuning &t, float ms, of_tuning *o)
     o->blocks_per_sm = t.blocks_per_sm;
     o->phased = t.phased;
     o->prefetch = t.prefetch;
+    o->tile_h = t.tile_h ? t.tile_h : LK_TH;
     o->ms = ms;
 }
 
@@ -109,6 +103,7 @@ int of_tuning_set(const of_plan *method, int32_t size_class, const of_tuning *t)
     v.blocks_per_sm = t->blocks_per_sm;
     v.phased = t->phased;
     v.prefetch = t->prefetch;
+    v.tile_h = t->tile_h == LK_TH ? 0 : t->tile_h;
     if (!valid(v)) return OF_EINVAL;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_table[key_of(*method, size_class)] = v;
@@ -134,23 +129,28 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
     const of_plan &p0 = hs[0]->plan;
     // candidates: the grouped fixed-radius sums (gathered or staged I2) when the radius
     // has a specialised kernel, the per-output sums of the run-time-radius kernel; each
-    // as phase launches with no L2 prefetch or one 1 or 3 blocks per SM ahead, and as the
-    // persistent launch at full occupancy and at 2 and 1 blocks per SM
+    // as phase launches with no L2 prefetch or one 1 or 3 blocks per SM ahead (the grouped
+    // sums also with the other tile height), and as the persistent launch at full
+    // occupancy and at 2 and 1 blocks per SM
     std::vector<Tuning> cand;
     const int occ[6] = {-1, -2, -3, 0, 2, 1};   // < 0: phase launches with prefetch pf_of[-1 - b]
     const int pf_of[3] = {0, 1, 3};
-    for (int gs = radius_is_specialised(p0.radius) ? 0 : 1; gs <= 1; ++gs)
+    const bool variant = (p0.flags & OF_FLAG_I1GRAD) != 0;
+    for (int gs = radius_specialised(p0.radius) ? 0 : 1; gs <= 1; ++gs)
         for (int sg = 0; sg <= (gs ? 0 : 1); ++sg)
-            for (int b : occ) {
-                if ((p0.flags & OF_FLAG_I1GRAD) && (b >= 0 || sg)) continue;   // phase launches, gathered taps only
-                Tuning t;
-                t.generic_sums = gs;
-                t.stage_i2 = sg;
-                t.phased = b < 0 ? 1 : 0;
-                t.blocks_per_sm = b < 0 ? 0 : b;
-                t.prefetch = b < 0 ? pf_of[-1 - b] : 0;
-                cand.push_back(t);
-            }
+            for (int th = 0; th <= ((gs || variant) ? 0 : 1); ++th)
+                for (int b : occ) {
+                    if (variant && (b >= 0 || sg)) continue;   // phase launches, gathered taps only
+                    if (th && b >= 0) continue;                // the persistent launch has one tile height
+                    Tuning t;
+                    t.generic_sums = gs;
+                    t.stage_i2 = sg;
+                    t.phased = b < 0 ? 1 : 0;
+                    t.blocks_per_sm = b < 0 ? 0 : b;
+                    t.prefetch = b < 0 ? pf_of[-1 - b] : 0;
+                    t.tile_h = th ? ALT_TH : 0;
+                    cand.push_back(t);
+                }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);

@@ -58,7 +58,8 @@ class Plan(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """of_tuning: how a batched launch runs (see include/of.h)."""
     _fields_ = [("generic_sums", ctypes.c_int32), ("stage_i2", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("phased", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("phased", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -317,9 +318,10 @@ def tuning_get(method: Plan, size_class: int) -> dict | None:
     return t.as_dict()
 
 
-def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=0, blocks_per_sm=0, phased=1, prefetch=0):
+def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=0, blocks_per_sm=0, phased=1, prefetch=0,
+               tile_h=0):
     """of_tuning_set; the defaults are the library's tuning without a table entry."""
-    t = Tuning(int(generic_sums), int(stage_i2), int(blocks_per_sm), int(phased), int(prefetch), 0.0)
+    t = Tuning(int(generic_sums), int(stage_i2), int(blocks_per_sm), int(phased), int(prefetch), int(tile_h), 0.0)
     _check(_lib.of_tuning_set(ctypes.byref(method), int(size_class), ctypes.byref(t)), "of_tuning_set")
 
 

@@ -107,8 +107,16 @@ def test_tuning_table_host_calls(of):
         of.tuning_set(m, 20, prefetch=17)
     with pytest.raises(of.OfError):
         of.tuning_set(m, 20, blocks_per_sm=2, phased=1)                   # occupancy is a persistent-launch knob
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, tile_h=24)                                   # tile heights 20 and 32 only
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, tile_h=32, phased=0)                         # the persistent launch has one
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, tile_h=32, generic_sums=1)                   # the taller tile is grouped-sums only
+    of.tuning_set(m, 20, tile_h=32, prefetch=1)
+    assert (of.tuning_get(m, 20)["tile_h"], of.tuning_get(m, 20)["prefetch"]) == (32, 1)
     of.tuning_set(m, 20)
     t = of.tuning_get(m, 20)
-    assert (t["phased"], t["prefetch"]) == (1, 0)
+    assert (t["phased"], t["prefetch"], t["tile_h"]) == (1, 0, 20)
     of.tuning_clear()
     assert of.tuning_get(m, 20) is None
