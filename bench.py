@@ -256,6 +256,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the single-pair and e2e legs")
     ap.add_argument("--no-autotune", action="store_true", help="run the batched launch with the default tuning")
+    ap.add_argument("--branches", type=int, default=0,
+                    help="with --no-autotune: the default tuning in this many concurrent launch sequences")
     ap.add_argument("--i1grad", action="store_true",
                     help="time the first-image-gradient variant (window matrix fixed per level) as the step")
     ap.add_argument("--table1", action="store_true",
@@ -308,6 +310,8 @@ def main():
     if not args.no_autotune:
         from paper_1306_2461_gb300 import autotune
         tuning = autotune.tune(flows, I1, I2, us, vs, stream=stream, reps=2, save=False)
+    elif args.branches > 1:
+        of.tuning_set(flows[0].plan, of.batch_size_class(flows), branches=args.branches)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -358,7 +362,12 @@ def main():
         return 0
     alg, alg_pyr, alg_it = (algorithmic_bytes_i1grad if args.i1grad else algorithmic_bytes)(H, W, LEVELS, ITERS, 2, 2)
     phased = tuning["best"]["phased"] if tuning else 1
-    groups = (B + 63) // 64
+    branches = (tuning["best"]["branches"] if tuning else max(args.branches, 1)) if phased else 1
+    # the batch runs as `branches` concurrent sequences over runs of equal-size pairs (run k
+    # ends at the first pair count >= B k / branches), each in launches of at most 64 pairs
+    nb = min(branches, B)
+    cuts = [0] + [-(-B * k // nb) for k in range(1, nb)] + [B]
+    groups = sum((cuts[k + 1] - cuts[k] + 63) // 64 for k in range(nb))
     if args.i1grad:
         launches_per_step = groups * (max(LEVELS - 1, 1) + LEVELS + LEVELS * ITERS)
         step_kernels = (f"batch step: {groups * max(LEVELS - 1, 1)} phase_pyr_kernel + {groups * LEVELS} "
@@ -383,13 +392,14 @@ def main():
                    "method": ("first-image-gradient variant (window matrix fixed per level)" if args.i1grad
                               else "second-image gradient at the displaced position"),
                    "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased",
-                                                               "prefetch", "tile_h")}
-                              if tuning else "default (autotuner off)"),
+                                                               "prefetch", "tile_h", "branches")}
+                              if tuning else ("default (autotuner off)" if args.branches <= 1 else
+                                              f"default in {args.branches} concurrent sequences (autotuner off)")),
                    "l2": "no flush: per-step working set ~%.1f GB >> 129 MB L2" % (
                        B * (of.workspace_bytes(plan16) + 4 * H * W) / 1e9),
                    "parallelism": f"replicas x{world}"},
         "autotune_candidates_ms": ([[c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"], c["prefetch"],
-                                     c["tile_h"], round(c["ms"], 3)]
+                                     c["tile_h"], c["branches"], round(c["ms"], 3)]
                                     for c in tuning["candidates"]] if tuning else None),
         "latency_ms": {"step_p50": percentile(step_ms, 50), "step_p99": percentile(step_ms, 99),
                        "step_max": max(step_ms)},
@@ -501,7 +511,8 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
         of.compute_batch_host(flows, h1, h2, hu, hv, I1, I2, us, vs, stream=stream, chunk=0)
 
     Ke = max(3, args.steps // 2)
-    for key, fn, path in (("e2e", e2e_pipelined, "pinned host frames -> of_compute_batch_host (6 chunks; uploads and "
+    for key, fn, path in (("e2e", e2e_pipelined, "pinned host frames -> of_compute_batch_host (default chunks of 3 pairs, "
+                                                 "alternating between two compute streams; uploads and "
                                                  "downloads on two copy streams overlap the launches) -> pinned host u, v"),
                           ("e2e_unpipelined", e2e_serial, "pinned host frames -> of_compute_batch -> pinned host u, v, "
                                                           "copies and launch in order on one stream")):

@@ -151,11 +151,14 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
 
 /*
  * of_compute_batch from and to HOST buffers, with the copies overlapped with the
- * computation. The pairs are taken in chunks of `chunk` pairs (0: six chunks): chunk
+ * computation. The pairs are taken in chunks of `chunk` pairs (0: about 3 Mpx of level 0
+ * per chunk, i.e. three 1024^2 pairs, and at most 24 chunks): chunk
  * k's frames are uploaded (hI1s/hI2s -> dI1s/dI2s) on an internal stream, its
- * batched launch runs on `stream` after that upload, and its fields are downloaded
- * (dus/dvs -> hus/hvs) on a second internal stream after the launch, so the uploads
- * and downloads of neighbouring chunks overlap the launches. hI1s[i] == NULL reuses
+ * batched launch runs after that upload (even chunks on `stream`, odd chunks on a
+ * compute stream the library keeps per device for the life of the process, so that
+ * neighbouring chunks' launches overlap), and its fields are downloaded (dus/dvs ->
+ * hus/hvs) on a second internal stream after the launch, so the uploads and downloads
+ * of neighbouring chunks overlap the launches. hI1s[i] == NULL reuses
  * the previous pyramid (dI1s[i] is then ignored). Host buffers should be pinned (page-
  * locked) for the copies to be asynchronous; device buffers are caller-owned, sized
  * as in of_compute. The call is complete (fields in hus/hvs) when `stream` reaches it.
@@ -171,7 +174,8 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  * batch shape has the same results to within the stated tolerances whichever tuning
  * runs it; with grouped sums (generic_sums == 0) they are the results of of_compute bit
  * for bit (with the default tile height). Without a table entry a batch runs
- * {generic_sums 0, stage_i2 0, blocks_per_sm 0, phased 1, prefetch 0, tile_h 20}. A tuning:
+ * {generic_sums 0, stage_i2 0, blocks_per_sm 0, phased 1, prefetch 0, tile_h 20, branches 1}.
+ * A tuning:
  *   generic_sums   1: per-output window sums of the run-time-radius kernel;
  *                  0: grouped sums of the kernel specialised for the radius
  *   stage_i2       1: stage I2 footprints in shared memory (specialised kernel only)
@@ -186,6 +190,11 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  *                  20 (the default; 0 means the default) or 32. Tiles other than the
  *                  default move each tile's reference flow, so their fields differ from
  *                  of_compute's by rounding (within the stated tolerances)
+ *   branches       phase launches: the pairs split into this many groups of about equal
+ *                  pixel counts whose launch sequences run concurrently (forked from and
+ *                  joined back into the caller's stream, inside the captured graph), so
+ *                  that one group's launches fill the last waves of another's; 1 to 4
+ *                  (0 means 1). Each pair's arithmetic is unchanged.
  *   ms             measured milliseconds per batch (of_autotune_batch output only)
  * The process-wide table is keyed by the method (in_format, storage, radius, levels,
  * iterations, OF_FLAG_ZNSSD) and a size class, round(log2(mean level-0 pixels per pair)).
@@ -197,6 +206,7 @@ typedef struct of_tuning {
     int32_t phased;
     int32_t prefetch;
     int32_t tile_h;
+    int32_t branches;
     float ms;
 } of_tuning;
 

@@ -2,8 +2,9 @@
 
 libof keeps a process-wide table, keyed by the method and the batch's size class, of
 how a batched launch runs: the window-sum strategy, I2 staging, the iteration tile's
-height, and phase launches (with or without an L2 prefetch) or the persistent launch at
-some resident blocks per SM (of_tuning in include/of.h). of_autotune_batch fills an entry by timing every
+height, and phase launches (with or without an L2 prefetch, in one or several concurrent
+sequences) or the persistent launch at some resident blocks per SM (of_tuning in
+include/of.h). of_autotune_batch fills an entry by timing every
 candidate on a real batch. This module keeps those entries in a JSON file per GPU
 model, so that a later process starts from the measured choice:
 
@@ -69,7 +70,8 @@ def load(path: str | None = None) -> int:
     for ent in data.values():
         b = ent["best"]
         of.tuning_set(_plan_of(ent["method"]), ent["size_class"], b["generic_sums"], b["stage_i2"],
-                      b["blocks_per_sm"], b.get("phased", 0), b.get("prefetch", 0), b.get("tile_h", 0))
+                      b["blocks_per_sm"], b.get("phased", 0), b.get("prefetch", 0), b.get("tile_h", 0),
+                      b.get("branches", 0))
     return len(data)
 
 

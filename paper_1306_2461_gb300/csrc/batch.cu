@@ -2,9 +2,11 @@
 // Sect. 3.3) in ONE persistent cooperative launch, replayed from a CUDA graph. The
 // kernel and its barrier are in batch_device.cuh; this file builds the work lists,
 // caches the captured launches and records the handles' state.
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -48,7 +50,7 @@ struct BatchEntry {
     Tuning tuning;
 };
 
-constexpr int BATCH_CACHE = 8;
+constexpr int BATCH_CACHE = 64;   // captured batches kept (a host pipeline call takes one per chunk)
 std::mutex g_mu;
 BatchEntry g_cache[BATCH_CACHE];
 uint64_t g_clock = 0;
@@ -240,10 +242,9 @@ static Resolved resolve(const of_plan &p0, const Tuning &t)
 // up to PHASE_PAIRS pairs (the per-pair arguments are kernel parameters): pyramid passes
 // (after the normalisation of Eq. 2 when the plan asks for it), then the iterations
 // level by level. Stream order separates the phases; there is no grid-wide barrier.
-static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_plan &p0, const Tuning &t,
-                                  cudaStream_t st)
+static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p0, const Tuning &t,
+                                 cudaStream_t st)
 {
-    const int n = (int)pairs.size();
     const int L = p0.levels;
     const bool zn = (p0.flags & OF_FLAG_ZNSSD) != 0;
     const int32_t stage = (!t.generic_sums && ((p0.flags & OF_FLAG_STAGE_I2) || t.stage_i2)) ? 1 : 0;
@@ -257,7 +258,7 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
     cudaError_t e;
     for (int g0 = 0; g0 < n; g0 += PHASE_PAIRS) {
         const int m = n - g0 < PHASE_PAIRS ? n - g0 : PHASE_PAIRS;
-        const BatchPair *bp = pairs.data() + g0;
+        const BatchPair *bp = pairs + g0;
         if (zn) {
             ZnPhase Z;
             memset(&Z, 0, sizeof(Z));
@@ -380,6 +381,76 @@ static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_
     return cudaSuccess;
 }
 
+// Side streams and events of the concurrent launch sequences, per device for the life of
+// the process. Used by run_batch only, under g_mu, so one batch at a time forks on them.
+struct Forks {
+    cudaStream_t s[3] = {};
+    cudaEvent_t fork = nullptr, join[3] = {};
+};
+
+static Forks *forks_for_device()
+{
+    static std::map<int, Forks> all;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    auto it = all.find(dev);
+    if (it != all.end()) return &it->second;
+    Forks f;
+    bool ok = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < 3 && ok; ++b)
+        ok = cudaStreamCreateWithFlags(&f.s[b], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&f.join[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        if (f.fork) cudaEventDestroy(f.fork);
+        for (int b = 0; b < 3; ++b) {
+            if (f.s[b]) cudaStreamDestroy(f.s[b]);
+            if (f.join[b]) cudaEventDestroy(f.join[b]);
+        }
+        return nullptr;
+    }
+    return &(all[dev] = f);
+}
+
+// The phase launches of a batch on `st`. With branches > 1 the pairs are split into that
+// many runs of about equal level-0 pixel counts whose launch sequences are forked from
+// `st` onto side streams and joined back (inside a capture they become parallel branches
+// of one graph): each run's launches fill the last waves of the others'.
+static cudaError_t enqueue_phased(const std::vector<BatchPair> &pairs, const of_plan &p0, const Tuning &t,
+                                  cudaStream_t st, int branches)
+{
+    const int n = (int)pairs.size();
+    const int nb = branches < n ? branches : n;
+    if (nb <= 1) return enqueue_chain(pairs.data(), n, p0, t, st);
+    Forks *f = forks_for_device();
+    if (!f) return cudaErrorUnknown;
+    double total = 0.0;
+    for (const BatchPair &bp : pairs) total += (double)bp.H[0] * bp.W[0];
+    int bound[5] = {0};
+    {
+        double acc = 0.0;
+        int k = 1;
+        for (int i = 0; i < n && k < nb; ++i) {
+            acc += (double)pairs[i].H[0] * pairs[i].W[0];
+            // run k - 1 ends after pair i once it holds its share; every run keeps a pair
+            if (acc >= total * k / nb && i + 1 >= k && n - (i + 1) >= nb - k) bound[k++] = i + 1;
+        }
+        for (; k < nb; ++k) bound[k] = bound[k - 1] + 1;   // shares not reached: one pair each
+        bound[nb] = n;
+    }
+    cudaError_t e = cudaEventRecord(f->fork, st);
+    for (int b = 1; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(f->s[b - 1], f->fork, 0);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b)
+        e = enqueue_chain(pairs.data() + bound[b], bound[b + 1] - bound[b], p0, t, b ? f->s[b - 1] : st);
+    // join every side stream, also after an error, so that no forked work is left unjoined
+    for (int b = 1; b < nb; ++b) {
+        const cudaError_t j = cudaEventRecord(f->join[b - 1], f->s[b - 1]) == cudaSuccess
+                                  ? cudaStreamWaitEvent(st, f->join[b - 1], 0)
+                                  : cudaErrorUnknown;
+        if (e == cudaSuccess) e = j;
+    }
+    return e;
+}
+
 // The variant with the first image's gradient runs as phase launches only (it has no
 // persistent form) and gathers its 4 taps (no staging).
 static Tuning effective(const of_plan &p0, Tuning t)
@@ -455,7 +526,7 @@ int batch_run_slot(BatchSlot &slot, int32_t n, const of_handle *hs, const void *
     memcpy(slot.host + pairs_bytes, b.prefix.data(), prefix_bytes);
     const Tuning t = effective(p0, tuning_for(p0, batch_size_class(n, hs)));
     if (t.phased) {
-        if (enqueue_phased(b.pairs, p0, t, st) != cudaSuccess || cudaEventRecord(slot.done, st) != cudaSuccess)
+        if (enqueue_phased(b.pairs, p0, t, st, 1) != cudaSuccess || cudaEventRecord(slot.done, st) != cudaSuccess)
             return OF_ECUDA;
         return commit_state(n, hs, b, st);
     }
@@ -501,16 +572,17 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
     if (rc) return rc;
     const of_plan &p0 = hs[0]->plan;
     const size_t pairs_bytes = sizeof(BatchPair) * n, prefix_bytes = sizeof(int32_t) * b.prefix.size();
-    std::vector<char> key(pairs_bytes + prefix_bytes + sizeof(st) + 6 * sizeof(int));
+    std::vector<char> key(pairs_bytes + prefix_bytes + sizeof(st) + 7 * sizeof(int));
     {
         char *k = key.data();
         memcpy(k, b.pairs.data(), pairs_bytes);
         memcpy(k + pairs_bytes, b.prefix.data(), prefix_bytes);
         memcpy(k + pairs_bytes + prefix_bytes, &st, sizeof(st));
-        const int extra[6] = {p0.radius,
+        const int extra[7] = {p0.radius,
                               (int)(p0.iterations * 16 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD))),
                               hs[0]->device, t.generic_sums, t.stage_i2,
-                              t.blocks_per_sm + 256 * t.phased + 65536 * t.prefetch + (1 << 24) * (t.tile_h != 0)};
+                              t.blocks_per_sm + 256 * t.phased + 65536 * t.prefetch + (1 << 24) * (t.tile_h != 0),
+                              t.phased ? t.branches : 0};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
 
@@ -562,7 +634,8 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
         if (graphs) {
             cudaGraph_t g = nullptr;
             if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                const cudaError_t le = ne.phased ? enqueue_phased(ne.pairs, ne.plan, ne.tuning, st) : launch_direct(ne, st);
+                const cudaError_t le = ne.phased ? enqueue_phased(ne.pairs, ne.plan, ne.tuning, st, ne.tuning.branches)
+                                                 : launch_direct(ne, st);
                 const cudaError_t ce = cudaStreamEndCapture(st, &g);
                 if (le == cudaSuccess && ce == cudaSuccess && g &&
                     cudaGraphInstantiate(&ne.exec, g, 0) != cudaSuccess)
@@ -575,7 +648,8 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
     }
     e->last_use = g_clock;
     cudaError_t err = e->exec ? cudaGraphLaunch(e->exec, st)
-                              : (e->phased ? enqueue_phased(e->pairs, e->plan, e->tuning, st) : launch_direct(*e, st));
+                              : (e->phased ? enqueue_phased(e->pairs, e->plan, e->tuning, st, e->tuning.branches)
+                                           : launch_direct(*e, st));
     if (err != cudaSuccess) return OF_ECUDA;
     if (cudaEventRecord(e->done, st) != cudaSuccess) return OF_ECUDA;
     return commit_state(n, hs, b, st);
@@ -594,11 +668,31 @@ extern "C" int of_compute_batch(int32_t n, const of_handle *hs, const void *cons
 
 // ------------------------------------------------------ host-buffer pipelined form
 // of_compute_batch_host: the batch in chunks; chunk k's upload runs on a copy stream,
-// its persistent launch on the caller's stream after that upload, and its download on a
-// second copy stream after the launch, so that uploads, launches and downloads of
-// neighbouring chunks overlap. Events order the three streams; the caller's stream
-// waits for the last download before the call's completion.
+// its launches after that upload on one of two compute streams (the caller's for even
+// chunks, the pipeline's own for odd ones), and its download on a second copy stream
+// after the launches, so that uploads, launches and downloads of neighbouring chunks
+// overlap and one chunk's launches fill the last, partly empty waves of the other's.
+// Events order the four streams; the caller's stream waits for the last download
+// before the call's completion.
 namespace {
+
+// The pipeline's compute stream on the current device, kept for the life of the process:
+// captured launches are cached per stream, so it must outlive a call for the next call
+// to replay them.
+cudaStream_t pipe_compute_stream()
+{
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = streams.find(dev);
+    if (it != streams.end()) return it->second;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    streams[dev] = s;
+    return s;
+}
 
 struct HostPipe {
     cudaStream_t up = nullptr, down = nullptr;
@@ -638,16 +732,27 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
             return OF_EINVAL;
         if (!hI1s[i] && !hs[i]->has_prev) return OF_ESTATE;
     }
-    const int per = chunk > 0 ? chunk : (n + 5) / 6;   // default: six chunks (measured best of 2-8)
+    // default: chunks of about three 1024^2 pairs (measured on 64 such pairs: 3 pairs per
+    // chunk beat 4, 6, 8 and 11), at most 24 chunks
+    int per = chunk;
+    if (per <= 0) {
+        double px = 0.0;
+        for (int i = 0; i < n; ++i) px += (double)hs[i]->plan.H * hs[i]->plan.W;
+        per = (int)lround(3.0 * 1048576.0 / (px / n));
+        per = std::max(per, std::max(1, (n + 23) / 24));
+    }
     const int nch = (n + per - 1) / per;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t aux = nch > 1 ? pipe_compute_stream() : st;
+    if (!aux) return OF_ECUDA;
     HostPipe pp;
     if (cudaStreamCreateWithFlags(&pp.up, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&pp.down, cudaStreamNonBlocking) != cudaSuccess)
         return OF_ECUDA;
     cudaEvent_t start = pp.make();
     if (!start || cudaEventRecord(start, st) != cudaSuccess || cudaStreamWaitEvent(pp.up, start, 0) != cudaSuccess ||
-        cudaStreamWaitEvent(pp.down, start, 0) != cudaSuccess)
+        cudaStreamWaitEvent(pp.down, start, 0) != cudaSuccess ||
+        (aux != st && cudaStreamWaitEvent(aux, start, 0) != cudaSuccess))
         return OF_ECUDA;
     const size_t in_elem = hs[0]->plan.in_format == OF_U8 ? 1 : 2;
     std::vector<const void *> d1(per);
@@ -660,13 +765,14 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
                 return OF_ECUDA;
             d1[i - off] = hI1s[i] ? dI1s[i] : nullptr;
         }
+        cudaStream_t cs = (c & 1) ? aux : st;
         cudaEvent_t in = pp.make(), done = pp.make();
-        if (!in || !done || cudaEventRecord(in, pp.up) != cudaSuccess || cudaStreamWaitEvent(st, in, 0) != cudaSuccess)
+        if (!in || !done || cudaEventRecord(in, pp.up) != cudaSuccess || cudaStreamWaitEvent(cs, in, 0) != cudaSuccess)
             return OF_ECUDA;
         const Tuning t = tuning_for(hs[0]->plan, batch_size_class(cnt, hs + off));
-        const int rc = run_batch(cnt, hs + off, d1.data(), dI2s + off, dus + off, dvs + off, st, t);
+        const int rc = run_batch(cnt, hs + off, d1.data(), dI2s + off, dus + off, dvs + off, cs, t);
         if (rc != OF_OK) return rc;
-        if (cudaEventRecord(done, st) != cudaSuccess || cudaStreamWaitEvent(pp.down, done, 0) != cudaSuccess)
+        if (cudaEventRecord(done, cs) != cudaSuccess || cudaStreamWaitEvent(pp.down, done, 0) != cudaSuccess)
             return OF_ECUDA;
         for (int i = off; i < off + cnt; ++i) {
             const size_t bytes = (size_t)hs[i]->plan.H * hs[i]->plan.W * sizeof(float);

@@ -78,6 +78,7 @@ struct Tuning {
     int phased = 1;          // 1: one ordinary launch per phase; 0: the persistent launch with grid barriers
     int prefetch = 0;        // phase launches: warm L2 for the tile this many blocks per SM ahead (0: off)
     int tile_h = 0;          // phase launches with grouped sums: iteration tile height (0: the default)
+    int branches = 0;        // phase launches: concurrent launch sequences over parts of the batch (0: one)
 };
 // The tuning table entry for this method and size class, or the default.
 Tuning tuning_for(const of_plan &method, int size_class);

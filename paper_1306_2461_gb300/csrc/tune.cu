@@ -34,7 +34,8 @@ bool valid(const Tuning &t)
     return t.generic_sums >= 0 && t.generic_sums <= 1 && t.stage_i2 >= 0 && t.stage_i2 <= 1 && t.blocks_per_sm >= 0 &&
            t.blocks_per_sm <= 64 && t.phased >= 0 && t.phased <= 1 && !(t.generic_sums && t.stage_i2) &&
            !(t.phased && t.blocks_per_sm) && t.prefetch >= 0 && t.prefetch <= 16 &&
-           (t.tile_h == 0 || t.tile_h == LK_TH || (t.tile_h == ALT_TH && t.phased && !t.generic_sums));
+           (t.tile_h == 0 || t.tile_h == LK_TH || (t.tile_h == ALT_TH && t.phased && !t.generic_sums)) &&
+           t.branches >= 0 && t.branches <= 4 && (t.branches <= 1 || t.phased);
 }
 
 void to_c(const Tuning &t, float ms, of_tuning *o)
@@ -45,6 +46,7 @@ void to_c(const Tuning &t, float ms, of_tuning *o)
     o->phased = t.phased;
     o->prefetch = t.prefetch;
     o->tile_h = t.tile_h ? t.tile_h : LK_TH;
+    o->branches = t.branches ? t.branches : 1;
     o->ms = ms;
 }
 
@@ -104,6 +106,7 @@ int of_tuning_set(const of_plan *method, int32_t size_class, const of_tuning *t)
     v.phased = t->phased;
     v.prefetch = t->prefetch;
     v.tile_h = t->tile_h == LK_TH ? 0 : t->tile_h;
+    v.branches = t->branches == 1 ? 0 : t->branches;
     if (!valid(v)) return OF_EINVAL;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_table[key_of(*method, size_class)] = v;
@@ -130,7 +133,8 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
     // candidates: the grouped fixed-radius sums (gathered or staged I2) when the radius
     // has a specialised kernel, the per-output sums of the run-time-radius kernel; each
     // as phase launches with no L2 prefetch or one 1 or 3 blocks per SM ahead (the grouped
-    // sums also with the other tile height), and as the persistent launch at full
+    // sums also with the other tile height; without prefetch also as two concurrent
+    // launch sequences over halves of the batch), and as the persistent launch at full
     // occupancy and at 2 and 1 blocks per SM
     std::vector<Tuning> cand;
     const int occ[6] = {-1, -2, -3, 0, 2, 1};   // < 0: phase launches with prefetch pf_of[-1 - b]
@@ -150,6 +154,10 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
                     t.prefetch = b < 0 ? pf_of[-1 - b] : 0;
                     t.tile_h = th ? ALT_TH : 0;
                     cand.push_back(t);
+                    if (t.phased && t.prefetch == 0 && n > 1) {
+                        t.branches = 2;
+                        cand.push_back(t);
+                    }
                 }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

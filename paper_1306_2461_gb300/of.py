@@ -59,7 +59,7 @@ class Tuning(ctypes.Structure):
     """of_tuning: how a batched launch runs (see include/of.h)."""
     _fields_ = [("generic_sums", ctypes.c_int32), ("stage_i2", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("phased", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("ms", ctypes.c_float)]
+                ("branches", ctypes.c_int32), ("ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -267,8 +267,8 @@ def _host_ptr(t: torch.Tensor | None, dtype, p: Plan, name: str) -> int | None:
 
 def compute_batch_host(flows, hI1s, hI2s, hus, hvs, dI1s, dI2s, dus, dvs, stream=None, chunk=0):
     """of_compute_batch_host: frames from host tensors, fields into host tensors, the
-    copies overlapped with the batched launches (chunks of `chunk` pairs, 0 = six
-    chunks). hI1s[i] = None reuses the previous pyramid. Synchronise `stream` before
+    copies overlapped with the batched launches (chunks of `chunk` pairs, 0 = about
+    3 Mpx per chunk). hI1s[i] = None reuses the previous pyramid. Synchronise `stream` before
     reading hus/hvs."""
     n = len(flows)
     img = [torch.uint8 if f.plan.in_format == OF_U8 else torch.uint16 for f in flows]
@@ -319,9 +319,10 @@ def tuning_get(method: Plan, size_class: int) -> dict | None:
 
 
 def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=0, blocks_per_sm=0, phased=1, prefetch=0,
-               tile_h=0):
+               tile_h=0, branches=0):
     """of_tuning_set; the defaults are the library's tuning without a table entry."""
-    t = Tuning(int(generic_sums), int(stage_i2), int(blocks_per_sm), int(phased), int(prefetch), int(tile_h), 0.0)
+    t = Tuning(int(generic_sums), int(stage_i2), int(blocks_per_sm), int(phased), int(prefetch), int(tile_h),
+               int(branches), 0.0)
     _check(_lib.of_tuning_set(ctypes.byref(method), int(size_class), ctypes.byref(t)), "of_tuning_set")
 
 

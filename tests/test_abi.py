@@ -113,10 +113,16 @@ def test_tuning_table_host_calls(of):
         of.tuning_set(m, 20, tile_h=32, phased=0)                         # the persistent launch has one
     with pytest.raises(of.OfError):
         of.tuning_set(m, 20, tile_h=32, generic_sums=1)                   # the taller tile is grouped-sums only
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, branches=5)                                  # at most 4 concurrent sequences
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, branches=2, phased=0)                        # a phase-launch knob
+    of.tuning_set(m, 20, branches=3)
+    assert of.tuning_get(m, 20)["branches"] == 3
     of.tuning_set(m, 20, tile_h=32, prefetch=1)
     assert (of.tuning_get(m, 20)["tile_h"], of.tuning_get(m, 20)["prefetch"]) == (32, 1)
     of.tuning_set(m, 20)
     t = of.tuning_get(m, 20)
-    assert (t["phased"], t["prefetch"], t["tile_h"]) == (1, 0, 20)
+    assert (t["phased"], t["prefetch"], t["tile_h"], t["branches"]) == (1, 0, 20, 1)
     of.tuning_clear()
     assert of.tuning_get(m, 20) is None

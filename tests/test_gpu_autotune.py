@@ -43,10 +43,11 @@ def test_every_candidate_matches_the_per_pair_path(of, oracle_mod):
     torch.cuda.synchronize()
     best, cands = of.autotune_batch(flows, I1, I2, reps=2)
     print(best, cands)
-    assert len(cands) == 24 and best["ms"] == min(c["ms"] for c in cands)
+    assert len(cands) == 29 and best["ms"] == min(c["ms"] for c in cands)
+    assert sum(c["branches"] == 2 for c in cands) == 5
     sc = of.batch_size_class(flows)
     t = of.tuning_get(flows[0].plan, sc)
-    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h")
+    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches")
     assert tuple(t[k] for k in keys) == tuple(best[k] for k in keys)
     for c in cands:
         of.tuning_set(flows[0].plan, sc, *(c[k] for k in keys))
@@ -75,18 +76,80 @@ def test_cache_file_round_trip(of, tmp_path):
     path = str(tmp_path / "tune.json")
     ent = autotune.tune(flows, I1, I2, reps=1, path=path)
     sc = of.batch_size_class(flows)
-    assert ent["size_class"] == sc and len(ent["candidates"]) == 24
+    assert ent["size_class"] == sc and len(ent["candidates"]) == 29
     of.tuning_clear()
     assert of.tuning_get(flows[0].plan, sc) is None
     assert autotune.load(path) == 1
     t = of.tuning_get(flows[0].plan, sc)
-    assert (t["generic_sums"], t["stage_i2"], t["blocks_per_sm"], t["phased"]) == \
-        (ent["best"]["generic_sums"], ent["best"]["stage_i2"], ent["best"]["blocks_per_sm"], ent["best"]["phased"])
+    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches")
+    assert tuple(t[k] for k in keys) == tuple(ent["best"][k] for k in keys)
     again = autotune.ensure(flows, I1, I2, path=path)      # known: no new timing
     assert again["candidates"] == [] and again["best"]["generic_sums"] == ent["best"]["generic_sums"]
     of.tuning_clear()
     for f in flows:
         f.close()
+
+
+@pytest.mark.parametrize("r", [2, 3, 4, 5, 6, 8, 10])
+def test_tall_tile_every_radius_ragged(of, oracle_mod, r):
+    """The 64 x 32 iteration tile, gathered and staged I2, on sizes that leave partial
+    tiles at the bottom and the right, for every radius with a fixed-radius kernel:
+    within the FP32 tolerance of the per-pair path (64 x 20 tiles) and of the oracle."""
+    import torch
+    sizes = [(97, 130), (200, 333)]
+    pairs = [synth.make_c1(H, W, seed=40 + k) for k, (H, W) in enumerate(sizes)]
+    flows = [of.Flow(of.Plan.make(H, W, 2, r, 2, bits=8, storage="f32")) for H, W in sizes]
+    I1 = [to_dev(p.I1) for p in pairs]
+    I2 = [to_dev(p.I2) for p in pairs]
+    ref = []
+    for k, (H, W) in enumerate(sizes):
+        with of.Flow(of.Plan.make(H, W, 2, r, 2, bits=8, storage="f32")) as f:
+            u, v = f.compute(I1[k], I2[k])
+            ref.append((u.clone(), v.clone()))
+    sc = of.batch_size_class(flows)
+    for stage in (0, 1):
+        of.tuning_set(flows[0].plan, sc, stage_i2=stage, tile_h=32)
+        assert of.tuning_get(flows[0].plan, sc)["tile_h"] == 32
+        us, vs = of.compute_batch(flows, I1, I2)
+        torch.cuda.synchronize()
+        for f in flows:
+            assert f.sync_status() == of.OF_OK
+        m = (r + 2) * 2
+        for k in range(len(sizes)):
+            d = max(float((us[k] - ref[k][0])[m:-m, m:-m].abs().max()),
+                    float((vs[k] - ref[k][1])[m:-m, m:-m].abs().max()))
+            assert d <= 1e-3, (r, stage, k, d)
+            assert bool(torch.isfinite(us[k]).all()) and bool(torch.isfinite(vs[k]).all())
+        parity_check(us[1].cpu().double().numpy(), vs[1].cpu().double().numpy(), pairs[1], oracle_mod, 2, r, 2,
+                     "f32", f"64x32 tiles, r {r}, staged {stage}")
+    of.tuning_clear()
+    for f in flows:
+        f.close()
+
+
+@pytest.mark.parametrize("branches", [2, 3, 4])
+def test_concurrent_sequences_match_single_pairs(of, branches):
+    """Phase launches split into concurrent sequences over parts of a mixed-size batch
+    (fewer pairs than sequences included), also reusing the previous pyramids: the
+    per-pair results bit for bit."""
+    import torch
+    for sizes in ([(256, 256), (64, 96), (192, 320), (128, 128), (97, 130)], [(130, 97), (256, 192)]):
+        pairs, flows, I1, I2 = batch(of, sizes, storage="f16", seed=60)
+        alone = [of.Flow(of.Plan.make(H, W, 3, 4, 3, bits=8, storage="f16")) for H, W in sizes]
+        sc = of.batch_size_class(flows)
+        of.tuning_set(flows[0].plan, sc, branches=branches)
+        assert of.tuning_get(flows[0].plan, sc)["branches"] == branches
+        for step in range(2):
+            first = I1 if step == 0 else [None] * len(sizes)
+            second = I2 if step == 0 else I1      # the next frame: the reused pyramid is I2's
+            us, vs = of.compute_batch(flows, first, second)
+            torch.cuda.synchronize()
+            for k, f in enumerate(alone):
+                u, v = f.compute(first[k], second[k])
+                assert torch.equal(us[k], u) and torch.equal(vs[k], v), (branches, sizes, step, k)
+        of.tuning_clear()
+        for f in flows + alone:
+            f.close()
 
 
 def test_autotune_refuses_reused_pyramids(of):

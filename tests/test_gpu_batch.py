@@ -169,11 +169,13 @@ def test_empty_and_degenerate_batches(of, oracle_mod):
         f.close()
 
 
+@pytest.mark.parametrize("branches", [1, 2])
 @pytest.mark.parametrize("chunk", [0, 1, 3, 64])
-def test_host_buffer_pipeline_equals_device_batch(of, chunk):
+def test_host_buffer_pipeline_equals_device_batch(of, chunk, branches):
     # frames from pinned host memory, fields back to pinned host memory, copies
-    # overlapped with the chunked launches: the same bits as of_compute_batch, including
-    # pairs that reuse their previous pyramid
+    # overlapped with the chunked launches (alternating between two compute streams, each
+    # chunk in one or two concurrent launch sequences): the same bits as
+    # of_compute_batch, including pairs that reuse their previous pyramid
     import torch
     from paper_1306_2461_gb300 import serve
     streams = [synth.ParticleStream(*hw, seed=20 + k) for k, hw in
@@ -187,6 +189,10 @@ def test_host_buffer_pipeline_equals_device_batch(of, chunk):
         frames.append(fr)
     n = len(streams)
     plans = [of.Plan.make(*fr[0].shape, 3, 4, 3, bits=12, storage="f16") for fr in frames]
+    of.tuning_clear()
+    if branches > 1:     # every size class a chunk of these pairs can have
+        for sc in range(8, 20):
+            of.tuning_set(plans[0], sc, branches=branches)
     fa = [of.Flow(p) for p in plans]
     fb = [of.Flow(p) for p in plans]
     hI = [[serve.pinned_frame(x) for x in fr] for fr in frames]
@@ -220,6 +226,7 @@ def test_host_buffer_pipeline_equals_device_batch(of, chunk):
                               dI1[:1] * 2, dI2[:1] * 2, du[:1] * 2, dv[:1] * 2, stream=s)
     for f in fa + fb:
         f.close()
+    of.tuning_clear()
 
 
 def test_more_pairs_than_one_phase_launch_holds(of):

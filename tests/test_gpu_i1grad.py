@@ -170,7 +170,8 @@ def test_batched_host_and_served_variant_equal_per_pair(of):
             u1, v1 = alone(k, j)
             assert torch.equal(outs[(k, j)][0], u1) and torch.equal(outs[(k, j)][1], v1), (k, j)
     best, cands = of.autotune_batch(flows, [to_dev(f[0]) for f in frames], [to_dev(f[1]) for f in frames], reps=1)
-    assert len(cands) == 6 and all(c["phased"] == 1 and c["stage_i2"] == 0 for c in cands)
+    assert len(cands) == 8 and all(c["phased"] == 1 and c["stage_i2"] == 0 for c in cands)
+    assert sum(c["branches"] == 2 for c in cands) == 2
     of.tuning_clear()
     for f in flows:
         f.close()
