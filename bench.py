@@ -439,9 +439,10 @@ def main():
 
 def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows, world=1):
     """Outside the headline timed region: the plain FP32 single-pair form (the comparison
-    the target names), the first-image-gradient variant, e2e through the C ABI with host
-    buffers (whole job over all ranks, like the headline), and the serving loop. The
-    single-pair, variant and serving legs are this rank's GPU alone."""
+    the target names), the first-image-gradient variant, the batch at FP32 storage, e2e
+    through the C ABI with host buffers (whole job over all ranks, like the headline),
+    and the serving loop. The single-pair, variant, FP32-batch and serving legs are this
+    rank's GPU alone."""
     out = {}
     K = max(args.steps, 20)
     # plain FP32 single pair, one of_compute (graph replay) per field; the same at FP16
@@ -490,6 +491,33 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
                                  "ms_per_step": a.elapsed_time(b) / Kv,
                                  "epe_vs_ground_truth_px": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}}
     for f in fv:
+        f.close()
+    # the same batch at FP32 storage of the reduced levels (autotuned like the headline)
+    plan32 = of.Plan.make(H, W, LEVELS, RADIUS, ITERS, bits=BITS, storage="f32")
+    f32 = [of.Flow(plan32) for _ in range(len(flows))]
+    t32 = None
+    if not args.no_autotune:
+        from paper_1306_2461_gb300 import autotune
+        t32 = autotune.tune(f32, I1, I2, us, vs, stream=stream, reps=2, save=False)["best"]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            of.compute_batch(f32, I1, I2, us, vs, stream=stream)
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        K32 = max(5, args.steps // 2)
+        a.record(stream)
+        for _ in range(K32):
+            of.compute_batch(f32, I1, I2, us, vs, stream=stream)
+        b.record(stream)
+        stream.synchronize()
+    e = np.sqrt((us[0].cpu().double().numpy() - src[0].u_gt) ** 2 +
+                (vs[0].cpu().double().numpy() - src[0].v_gt) ** 2)[m:-m, m:-m]
+    out["batched_f32"] = {"fields_per_s": len(f32) * K32 / (a.elapsed_time(b) / 1000.0),
+                          "ms_per_step": a.elapsed_time(b) / K32,
+                          "tuning": ({k: t32[k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased",
+                                                          "prefetch", "tile_h", "branches")} if t32 else None),
+                          "epe_vs_ground_truth_px": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}}
+    for f in f32:
         f.close()
     # e2e: host (pinned) frames in, device compute, host flow fields out, every step
     B = len(flows)
