@@ -76,9 +76,9 @@ def pixel_iterations(H, W, L, n):
 
 
 # Sources that take no part in the timed step (the serving loop, the allocation-free
-# entry point): left out of the hash, so that the recorded traffic stays attached to the
-# code that produced it.
-NOT_IN_STEP = {"server.cu", "noalloc.cu"}
+# entry point, the host-buffer pipeline): left out of the hash, so that the recorded
+# traffic stays attached to the code that produced it.
+NOT_IN_STEP = {"server.cu", "noalloc.cu", "host_pipe.cu"}
 
 
 def kernel_source_hash():

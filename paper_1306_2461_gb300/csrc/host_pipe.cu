@@ -1,0 +1,140 @@
+// of_compute_batch_host: of_compute_batch from and to host buffers, with the copies
+// overlapped with the launches (Sect. 3.3: the fields of a batch are independent, so the
+// pairs can be uploaded, computed and downloaded chunk by chunk).
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "of_engine.h"
+
+using namespace of;
+
+// ------------------------------------------------------ host-buffer pipelined form
+// of_compute_batch_host: the batch in chunks; chunk k's upload runs on a copy stream,
+// its launches after that upload on one of two compute streams (the caller's for even
+// chunks, the pipeline's own for odd ones), and its download on a second copy stream
+// after the launches, so that uploads, launches and downloads of neighbouring chunks
+// overlap and one chunk's launches fill the last, partly empty waves of the other's.
+// Events order the four streams; the caller's stream waits for the last download
+// before the call's completion.
+namespace {
+
+// The pipeline's compute stream of the calling thread on the current device, kept until
+// the thread exits: captured launches are cached per stream, so it must outlive a call
+// for the next call to replay them, and it is the thread's own, so that no other thread
+// queues work on it while a launch sequence is being captured there.
+struct PipeStreams {
+    std::map<int, cudaStream_t> s;
+    ~PipeStreams()
+    {
+        for (auto &kv : s) cudaStreamDestroy(kv.second);   // pending work still runs
+    }
+};
+
+cudaStream_t pipe_compute_stream()
+{
+    thread_local PipeStreams streams;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    auto it = streams.s.find(dev);
+    if (it != streams.s.end()) return it->second;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    streams.s[dev] = st;
+    return st;
+}
+
+struct HostPipe {
+    cudaStream_t up = nullptr, down = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~HostPipe()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);   // released once recorded work completes
+        if (up) cudaStreamDestroy(up);    // likewise: pending copies still run
+        if (down) cudaStreamDestroy(down);
+    }
+    cudaEvent_t make()
+    {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        ev.push_back(e);
+        return e;
+    }
+};
+
+}  // namespace
+
+extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1s, const void *const *hI2s,
+                                     float *const *hus, float *const *hvs, void *const *dI1s, void *const *dI2s,
+                                     float *const *dus, float *const *dvs, of_stream_t stream, int32_t chunk)
+{
+    if (n == 0) return OF_OK;
+    if (n < 0 || n > 65536 || !hs || !hI1s || !hI2s || !hus || !hvs || !dI1s || !dI2s || !dus || !dvs || chunk < 0)
+        return OF_EINVAL;
+    std::vector<of_handle> seen(hs, hs + n);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return OF_EINVAL;   // a handle twice
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || !hI2s[i] || !hus[i] || !hvs[i] || !dI2s[i] || !dus[i] || !dvs[i] || (hI1s[i] && !dI1s[i]))
+            return OF_EINVAL;
+        if (!same_method(hs[i]->plan, hs[0]->plan) || hs[i]->device != hs[0]->device)
+            return OF_EINVAL;
+        if (!hI1s[i] && !hs[i]->has_prev) return OF_ESTATE;
+    }
+    // default: chunks of about three 1024^2 pairs (measured on 64 such pairs: 3 pairs per
+    // chunk beat 4, 6, 8 and 11), at most 24 chunks
+    int per = chunk;
+    if (per <= 0) {
+        double px = 0.0;
+        for (int i = 0; i < n; ++i) px += (double)hs[i]->plan.H * hs[i]->plan.W;
+        per = (int)lround(3.0 * 1048576.0 / (px / n));
+        per = std::max(per, std::max(1, (n + 23) / 24));
+    }
+    const int nch = (n + per - 1) / per;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t aux = nch > 1 ? pipe_compute_stream() : st;
+    if (!aux) return OF_ECUDA;
+    HostPipe pp;
+    if (cudaStreamCreateWithFlags(&pp.up, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pp.down, cudaStreamNonBlocking) != cudaSuccess)
+        return OF_ECUDA;
+    cudaEvent_t start = pp.make();
+    if (!start || cudaEventRecord(start, st) != cudaSuccess || cudaStreamWaitEvent(pp.up, start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(pp.down, start, 0) != cudaSuccess ||
+        (aux != st && cudaStreamWaitEvent(aux, start, 0) != cudaSuccess))
+        return OF_ECUDA;
+    const size_t in_elem = hs[0]->plan.in_format == OF_U8 ? 1 : 2;
+    std::vector<const void *> d1(per);
+    for (int c = 0; c < nch; ++c) {
+        const int off = c * per, cnt = off + per <= n ? per : n - off;
+        for (int i = off; i < off + cnt; ++i) {
+            const size_t px = (size_t)hs[i]->plan.H * hs[i]->plan.W;
+            if ((hI1s[i] && cudaMemcpyAsync(dI1s[i], hI1s[i], px * in_elem, cudaMemcpyHostToDevice, pp.up) != cudaSuccess) ||
+                cudaMemcpyAsync(dI2s[i], hI2s[i], px * in_elem, cudaMemcpyHostToDevice, pp.up) != cudaSuccess)
+                return OF_ECUDA;
+            d1[i - off] = hI1s[i] ? dI1s[i] : nullptr;
+        }
+        cudaStream_t cs = (c & 1) ? aux : st;
+        cudaEvent_t in = pp.make(), done = pp.make();
+        if (!in || !done || cudaEventRecord(in, pp.up) != cudaSuccess || cudaStreamWaitEvent(cs, in, 0) != cudaSuccess)
+            return OF_ECUDA;
+        const Tuning t = tuning_for(hs[0]->plan, batch_size_class(cnt, hs + off));
+        const int rc = run_batch(cnt, hs + off, d1.data(), dI2s + off, dus + off, dvs + off, cs, t);
+        if (rc != OF_OK) return rc;
+        if (cudaEventRecord(done, cs) != cudaSuccess || cudaStreamWaitEvent(pp.down, done, 0) != cudaSuccess)
+            return OF_ECUDA;
+        for (int i = off; i < off + cnt; ++i) {
+            const size_t bytes = (size_t)hs[i]->plan.H * hs[i]->plan.W * sizeof(float);
+            if (cudaMemcpyAsync(hus[i], dus[i], bytes, cudaMemcpyDeviceToHost, pp.down) != cudaSuccess ||
+                cudaMemcpyAsync(hvs[i], dvs[i], bytes, cudaMemcpyDeviceToHost, pp.down) != cudaSuccess)
+                return OF_ECUDA;
+        }
+    }
+    cudaEvent_t end = pp.make();
+    if (!end || cudaEventRecord(end, pp.down) != cudaSuccess || cudaStreamWaitEvent(st, end, 0) != cudaSuccess)
+        return OF_ECUDA;
+    return OF_OK;
+}

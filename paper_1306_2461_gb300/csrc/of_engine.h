@@ -86,6 +86,8 @@ Tuning tuning_for(const of_plan &method, int size_class);
 int batch_size_class(int32_t n, const of_handle *hs);
 int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s, float *const *us,
               float *const *vs, cudaStream_t st, const Tuning &t);
+// Whether two plans can share a batched launch (same method; sizes may differ).
+bool same_method(const of_plan &a, const of_plan &b);
 
 struct BatchSlot {
     char *dev = nullptr;

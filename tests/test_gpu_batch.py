@@ -256,3 +256,55 @@ def test_more_pairs_than_one_phase_launch_holds(of):
         assert torch.equal(ub[k], u1) and torch.equal(vb[k], v1), k
     for f in flows:
         f.close()
+
+
+def test_host_pipelines_in_two_threads(of):
+    # two threads run host-buffer pipelines at once, each with its own handles, buffers and
+    # stream (and its own internal compute stream, on which its chunks' launch sequences are
+    # captured): every field equals the single-threaded device batch's
+    import threading
+    import torch
+    sizes = [(160, 224), (96, 128), (200, 136), (128, 128)]
+    n = len(sizes)
+    frames = [[synth.make_c1(H, W, seed=70 + 10 * t + k) for k, (H, W) in enumerate(sizes)] for t in range(2)]
+    plans = [of.Plan.make(H, W, 3, 4, 3, bits=8, storage="f16") for H, W in sizes]
+    results, errors = [None, None], []
+
+    def worker(t):
+        try:
+            fl = [of.Flow(p) for p in plans]
+            h1 = [torch.from_numpy(p.I1).pin_memory() for p in frames[t]]
+            h2 = [torch.from_numpy(p.I2).pin_memory() for p in frames[t]]
+            hu = [torch.empty(s, dtype=torch.float32).pin_memory() for s in sizes]
+            hv = [torch.empty(s, dtype=torch.float32).pin_memory() for s in sizes]
+            d1 = [torch.empty(s, dtype=torch.uint8, device="cuda") for s in sizes]
+            d2 = [torch.empty(s, dtype=torch.uint8, device="cuda") for s in sizes]
+            du = [torch.empty(s, dtype=torch.float32, device="cuda") for s in sizes]
+            dv = [torch.empty(s, dtype=torch.float32, device="cuda") for s in sizes]
+            s = torch.cuda.Stream()
+            for _ in range(20):
+                with torch.cuda.stream(s):
+                    of.compute_batch_host(fl, h1, h2, hu, hv, d1, d2, du, dv, stream=s, chunk=1)
+                s.synchronize()
+                for f in fl:
+                    assert f.sync_status() == of.OF_OK
+            results[t] = ([x.clone() for x in hu], [x.clone() for x in hv])
+            for f in fl:
+                f.close()
+        except Exception as e:      # reported by the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for t in range(2):
+        fb = [of.Flow(p) for p in plans]
+        ub, vb = of.compute_batch(fb, [to_dev(p.I1) for p in frames[t]], [to_dev(p.I2) for p in frames[t]])
+        torch.cuda.synchronize()
+        for k in range(n):
+            assert torch.equal(results[t][0][k], ub[k].cpu()) and torch.equal(results[t][1][k], vb[k].cpu()), (t, k)
+        for f in fb:
+            f.close()
