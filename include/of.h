@@ -155,10 +155,11 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
  * per chunk, i.e. three 1024^2 pairs, and at most 24 chunks): chunk
  * k's frames are uploaded (hI1s/hI2s -> dI1s/dI2s) on an internal stream, its
  * batched launch runs after that upload (even chunks on `stream`, odd chunks on a
- * compute stream the library keeps per device for the life of the process, so that
- * neighbouring chunks' launches overlap), and its fields are downloaded (dus/dvs ->
- * hus/hvs) on a second internal stream after the launch, so the uploads and downloads
- * of neighbouring chunks overlap the launches. hI1s[i] == NULL reuses
+ * compute stream the library keeps for the calling thread and device until the thread
+ * exits, so that neighbouring chunks' launches overlap), and its fields are downloaded
+ * (dus/dvs -> hus/hvs) on a second internal stream after the launch, so the uploads
+ * and downloads of neighbouring chunks overlap the launches. The copy streams are kept
+ * per thread and device as well. Calls from different threads are independent. hI1s[i] == NULL reuses
  * the previous pyramid (dI1s[i] is then ignored). Host buffers should be pinned (page-
  * locked) for the copies to be asynchronous; device buffers are caller-owned, sized
  * as in of_compute. The call is complete (fields in hus/hvs) when `stream` reaches it.

@@ -21,29 +21,42 @@ using namespace of;
 // before the call's completion.
 namespace {
 
-// The pipeline's compute stream of the calling thread on the current device, kept until
-// the thread exits: captured launches are cached per stream, so it must outlive a call
-// for the next call to replay them, and it is the thread's own, so that no other thread
-// queues work on it while a launch sequence is being captured there.
+// The pipeline's streams of the calling thread on the current device (the second compute
+// stream and the two copy streams), kept until the thread exits: captured launches are
+// cached per stream, so the compute stream must outlive a call for the next call to replay
+// them, and it is the thread's own, so that no other thread queues work on it while a
+// launch sequence is being captured there. Keeping the copy streams saves creating two
+// streams per call.
 struct PipeStreams {
-    std::map<int, cudaStream_t> s;
-    ~PipeStreams()
+    cudaStream_t compute = nullptr, up = nullptr, down = nullptr;
+};
+
+struct ThreadStreams {
+    std::map<int, PipeStreams> s;
+    ~ThreadStreams()
     {
-        for (auto &kv : s) cudaStreamDestroy(kv.second);   // pending work still runs
+        for (auto &kv : s)   // pending work still runs
+            for (cudaStream_t x : {kv.second.compute, kv.second.up, kv.second.down})
+                if (x) cudaStreamDestroy(x);
     }
 };
 
-cudaStream_t pipe_compute_stream()
+const PipeStreams *pipe_streams()
 {
-    thread_local PipeStreams streams;
+    thread_local ThreadStreams streams;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     auto it = streams.s.find(dev);
-    if (it != streams.s.end()) return it->second;
-    cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-    streams.s[dev] = st;
-    return st;
+    if (it != streams.s.end()) return &it->second;
+    PipeStreams p;
+    if (cudaStreamCreateWithFlags(&p.compute, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p.up, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p.down, cudaStreamNonBlocking) != cudaSuccess) {
+        for (cudaStream_t x : {p.compute, p.up, p.down})
+            if (x) cudaStreamDestroy(x);
+        return nullptr;
+    }
+    return &(streams.s[dev] = p);
 }
 
 struct HostPipe {
@@ -53,8 +66,6 @@ struct HostPipe {
     {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);   // released once recorded work completes
-        if (up) cudaStreamDestroy(up);    // likewise: pending copies still run
-        if (down) cudaStreamDestroy(down);
     }
     cudaEvent_t make()
     {
@@ -95,12 +106,12 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
     }
     const int nch = (n + per - 1) / per;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaStream_t aux = nch > 1 ? pipe_compute_stream() : st;
-    if (!aux) return OF_ECUDA;
+    const PipeStreams *ps = pipe_streams();
+    if (!ps) return OF_ECUDA;
+    cudaStream_t aux = nch > 1 ? ps->compute : st;
     HostPipe pp;
-    if (cudaStreamCreateWithFlags(&pp.up, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&pp.down, cudaStreamNonBlocking) != cudaSuccess)
-        return OF_ECUDA;
+    pp.up = ps->up;
+    pp.down = ps->down;
     cudaEvent_t start = pp.make();
     if (!start || cudaEventRecord(start, st) != cudaSuccess || cudaStreamWaitEvent(pp.up, start, 0) != cudaSuccess ||
         cudaStreamWaitEvent(pp.down, start, 0) != cudaSuccess ||

@@ -35,14 +35,18 @@ def oracle_check(oracle_mod, pair, u, v, L, r, n, storage):
                  f"{pair.I1.shape[0]}x{pair.I1.shape[1]}")
 
 
-def test_bench_configuration_full_size(of, oracle_mod):
+@pytest.mark.parametrize("branches", [1, 2])
+def test_bench_configuration_full_size(of, oracle_mod, branches):
     # 64 pairs of 1024^2 12-bit frames, FP16 storage, 3 levels, r = 4, 5 iterations:
-    # the launch the benchmark times (8 distinct pairs cycled, as there)
+    # the launch the benchmark times (8 distinct pairs cycled, as there), in one launch
+    # sequence (the default) and in the two concurrent sequences the autotuner picks
     import torch
     B, D = 64, 8
     src = [synth.make_c2(1024, 1024, seed=1 + 7919 * i) for i in range(D)]
     plan = of.Plan.make(1024, 1024, 3, 4, 5, bits=12, storage="f16")
     flows = [of.Flow(plan) for _ in range(B)]
+    of.tuning_clear()
+    of.tuning_set(plan, of.batch_size_class(flows), branches=branches)
     I1 = [to_dev(src[i % D].I1) for i in range(B)]
     I2 = [to_dev(src[i % D].I2) for i in range(B)]
     s = torch.cuda.Stream()
@@ -57,6 +61,7 @@ def test_bench_configuration_full_size(of, oracle_mod):
             assert torch.equal(us[j], u1) and torch.equal(vs[j], v1), j
     for i in (0, 5):
         oracle_check(oracle_mod, src[i], us[i], vs[i], 3, 4, 5, "f16")
+    of.tuning_clear()
     for f in flows:
         f.close()
 
