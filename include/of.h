@@ -198,7 +198,8 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  *                  (0 means 1). Each pair's arithmetic is unchanged.
  *   ms             measured milliseconds per batch (of_autotune_batch output only)
  * The process-wide table is keyed by the method (in_format, storage, radius, levels,
- * iterations, OF_FLAG_ZNSSD) and a size class, round(log2(mean level-0 pixels per pair)).
+ * iterations, OF_FLAG_ZNSSD, OF_FLAG_I1GRAD) and a size class, round(log2(mean level-0 pixels
+ * per pair)).
  */
 typedef struct of_tuning {
     int32_t generic_sums;

@@ -32,18 +32,20 @@ def _device() -> str:
 
 def _method(plan: of.Plan) -> dict:
     return {"in_format": plan.in_format, "in_bits": plan.in_bits, "storage": plan.storage, "radius": plan.radius,
-            "levels": plan.levels, "iterations": plan.iterations, "znssd": int(bool(plan.flags & of.OF_FLAG_ZNSSD))}
+            "levels": plan.levels, "iterations": plan.iterations, "znssd": int(bool(plan.flags & of.OF_FLAG_ZNSSD)),
+            "i1grad": int(bool(plan.flags & of.OF_FLAG_I1GRAD))}
 
 
 def _key(method: dict, size_class: int) -> str:
     m = method
     return (f"fmt{m['in_format']}/st{m['storage']}/r{m['radius']}/L{m['levels']}/n{m['iterations']}"
-            f"/zn{m['znssd']}/sc{size_class}")
+            f"/zn{m['znssd']}/i1{m.get('i1grad', 0)}/sc{size_class}")
 
 
 def _plan_of(method: dict) -> of.Plan:
+    flags = (of.OF_FLAG_ZNSSD if method["znssd"] else 0) | (of.OF_FLAG_I1GRAD if method.get("i1grad") else 0)
     p = of.Plan.make(64, 64, method["levels"], method["radius"], method["iterations"], bits=method["in_bits"],
-                     storage=method["storage"], flags=of.OF_FLAG_ZNSSD if method["znssd"] else 0)
+                     storage=method["storage"], flags=flags)
     p.in_format = method["in_format"]
     return p
 

@@ -1,5 +1,5 @@
 // The autotuner of the batched launch. A process-wide table maps a method (input
-// format, storage, radius, levels, iterations, normalisation) and a size class
+// format, storage, radius, levels, iterations, normalisation, variant) and a size class
 // (round(log2(mean level-0 pixels per pair))) to a Tuning: window-sum strategy, I2
 // staging, and either phase launches or the persistent launch at some resident blocks
 // per SM. of_compute_batch and the serving loop read it; of_autotune_batch fills it by
@@ -19,14 +19,21 @@ namespace of {
 
 namespace {
 
-using Key = std::array<int, 7>;
+using Key = std::array<int, 8>;
 
 std::mutex g_tune_mu;
 std::map<Key, Tuning> g_table;
 
 Key key_of(const of_plan &m, int size_class)
 {
-    return {m.in_format, m.storage, m.radius, m.levels, m.iterations, (m.flags & OF_FLAG_ZNSSD) ? 1 : 0, size_class};
+    return {m.in_format,
+            m.storage,
+            m.radius,
+            m.levels,
+            m.iterations,
+            (m.flags & OF_FLAG_ZNSSD) ? 1 : 0,
+            (m.flags & OF_FLAG_I1GRAD) ? 1 : 0,   // the variant runs other kernels
+            size_class};
 }
 
 bool valid(const Tuning &t)

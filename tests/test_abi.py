@@ -121,7 +121,11 @@ def test_tuning_table_host_calls(of):
     assert of.tuning_get(m, 20)["branches"] == 3
     of.tuning_set(m, 20, tile_h=32, prefetch=1)
     assert (of.tuning_get(m, 20)["tile_h"], of.tuning_get(m, 20)["prefetch"]) == (32, 1)
+    v = of.Plan.make(64, 64, 3, 4, 5, bits=12, storage="f16", flags=of.OF_FLAG_I1GRAD)
+    of.tuning_set(v, 20, branches=2)                                      # the variant keeps its own entry
+    assert of.tuning_get(v, 20)["branches"] == 2 and of.tuning_get(m, 20)["tile_h"] == 32
     of.tuning_set(m, 20)
+    assert of.tuning_get(v, 20)["branches"] == 2
     t = of.tuning_get(m, 20)
     assert (t["phased"], t["prefetch"], t["tile_h"], t["branches"]) == (1, 0, 20, 1)
     of.tuning_clear()
