@@ -36,6 +36,19 @@ MUTANTS = {
                                      "g1y[k] = (P1[(size_t)y * W + xp] - P1[(size_t)y * W + xm]) / 2.0;"),
     "guard_inverted": ("if (det <= OFO_SINGULAR_EPS * tr * tr) return 0;",
                        "if (det > OFO_SINGULAR_EPS * tr * tr) return 0;"),
+    "second_numerator_wrong_entry": ("*xv = (a * e0 - b * d0) / det;", "*xv = (c * e0 - b * d0) / det;"),
+    "window_rows_off_by_one": ("for (int dy = -r; dy <= r; ++dy) {", "for (int dy = -r; dy < r; ++dy) {"),
+    "vertical_gradient_sign": ("ofo_bilinear(I2, H, W, px, py + 1.0) - ofo_bilinear(I2, H, W, px, py - 1.0)",
+                               "ofo_bilinear(I2, H, W, px, py - 1.0) - ofo_bilinear(I2, H, W, px, py + 1.0)"),
+    "pyramid_keeps_odd_rows": ("const int y = clampi(2 * i + a - 2, 0, H - 1);",
+                               "const int y = clampi(2 * i + a - 1, 0, H - 1);"),
+    "pyramid_taps_flattened": ("{1.0, 4.0, 6.0, 4.0, 1.0}", "{2.0, 4.0, 4.0, 4.0, 2.0}"),
+    "normalisation_mean_not_subtracted": ("(I[(size_t)y * W + x] - mean) / sqrt(var + eps)",
+                                          "I[(size_t)y * W + x] / sqrt(var + eps)"),
+    "normalisation_printed_radicand": ("const double var = s2 / n - mean * mean;",
+                                       "const double var = mean * mean - s2 / n;"),
+    "sbubble_strict_threshold": ("if (u[k] <= Tv) ++c;", "if (u[k] < Tv) ++c;"),
+    "sbubble_threshold_not_halved": ("return 0.5 * ((double)lo + (double)hi);", "return ((double)lo + (double)hi);"),
 }
 
 
