@@ -35,3 +35,15 @@ def test_reference_arm_prints_one_json_line():
 def test_fewer_than_three_warmup_steps_are_refused():
     r = _bench("--warmup", "2", timeout=120)
     assert r.returncode != 0 and "--warmup must be >= 3" in r.stderr
+
+
+def test_pixel_iterations_per_field_of_the_workloads():
+    # n * sum_l N_l with N_l = ceil(H / 2^l) * ceil(W / 2^l): the unit of the reported
+    # Mpix*iter/s, for the 256^2 (2 levels, 4 iterations), 1024^2 (3, 5) and 2048^2 (4, 6)
+    # workloads, and a ragged size whose levels round up
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.pixel_iterations(256, 256, 2, 4) == 327_680
+    assert bench.pixel_iterations(1024, 1024, 3, 5) == 6_881_280
+    assert bench.pixel_iterations(2048, 2048, 4, 6) == 33_423_360
+    assert bench.pixel_iterations(383, 1791, 3, 1) == 383 * 1791 + 192 * 896 + 96 * 448
