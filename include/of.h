@@ -136,15 +136,16 @@ int of_compute(of_handle h, const void *I1, const void *I2, float *u, float *v, 
 /*
  * Compute n independent fields together (fields are independent, Sect. 3.3, so they
  * can share the GPU): one CUDA graph replay per call of either one launch per phase
- * (pyramid pass, one iteration of one level) over the tiles of up to 64 pairs, or one
- * persistent cooperative launch with bounded grid barriers between phases, as the
- * tuning table says (of_autotune_batch below). hs[i] are handles whose plans have
+ * (pyramid pass, one iteration of one level) over the tiles of up to 64 pairs, in one
+ * or several concurrent sequences over parts of the batch, or one persistent
+ * cooperative launch with bounded grid barriers between phases, as the tuning table
+ * says (of_autotune_batch below). hs[i] are handles whose plans have
  * equal levels, radius, iterations, in_format, in_bits, storage and method flags
  * (sizes may differ); a handle may appear at most once. I1s[i] may be NULL (reuse, as
  * in of_compute). All pointers as in of_compute. n == 0 is a no-op. OF_EINVAL on
  * mismatched plans, repeated handles or NULL pointers; OF_ESTATE as in of_compute.
  * The results are those of n separate of_compute calls (bit for bit with the grouped
- * window sums, the default).
+ * window sums and the default tile height, in any number of sequences).
  */
 int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void *const *I2s,
                      float *const *us, float *const *vs, of_stream_t stream);
