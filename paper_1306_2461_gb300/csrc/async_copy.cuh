@@ -1,6 +1,7 @@
-// Bulk asynchronous copies global -> shared (cp.async.bulk) completing on an mbarrier,
-// with a bounded wait. Used to stage the part of I2 a tile's warps read into shared
-// memory in one round of row copies.
+// Asynchronous copies global -> shared completing on an mbarrier, with a bounded wait:
+// untiled bulk copies (cp.async.bulk) and 2-D tiled tensor copies (cp.async.bulk.tensor,
+// the TMA unit) that stage an iteration tile's flow estimate and I2 window in shared
+// memory.
 #pragma once
 
 #include <stdint.h>
@@ -57,6 +58,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// One 2-D box of the tensor described by the tensor map at `map` (a kernel parameter:
+// param space) into shared memory at dst, completing on bar. (x, y) is the box's first
+// element; x times the element size must be a multiple of 16 bytes. Elements outside
+// the tensor (negative or beyond its extent) are written as zeros and still count
+// towards the box's bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)

@@ -179,8 +179,7 @@ static int build_batch(int32_t n, const of_handle *hs, const void *const *I1s, c
     return OF_OK;
 }
 
-static void fill_header(BatchHdr &hd, const of_plan &p0, const BatchBuild &b, char *dev, size_t bar_off,
-                        bool stage_i2)
+static void fill_header(BatchHdr &hd, const of_plan &p0, const BatchBuild &b, char *dev, size_t bar_off)
 {
     const size_t pairs_bytes = sizeof(BatchPair) * b.pairs.size();
     hd.pairs = reinterpret_cast<const BatchPair *>(dev);
@@ -195,7 +194,6 @@ static void fill_header(BatchHdr &hd, const of_plan &p0, const BatchBuild &b, ch
     hd.npyr = b.npyr;
     hd.fp64_cond = p0.fp64_cond;
     hd.timeout_ns = BARRIER_TIMEOUT_NS;
-    hd.stage_i2 = stage_i2 ? 1 : 0;
     hd.znssd = (p0.flags & OF_FLAG_ZNSSD) ? 1 : 0;
 }
 
@@ -219,11 +217,11 @@ static int grid_for(void *fn, size_t smem, int device, int max_items, int blocks
     return OF_OK;
 }
 
-// The kernel, shared memory and staging a tuning selects for a method.
+// The persistent kernel and its shared memory for a method (it gathers its taps: the
+// TMA staging of the phase launches needs tensor maps in parameter space).
 struct Resolved {
     void *fn;
     size_t smem;
-    bool stage;
 };
 static Resolved resolve(const of_plan &p0, const Tuning &t)
 {
@@ -231,11 +229,9 @@ static Resolved resolve(const of_plan &p0, const Tuning &t)
     if (t.generic_sums) {
         r.fn = batch_kernel_generic(p0.in_format, p0.storage);
         r.smem = batch_smem_generic(p0.radius);
-        r.stage = false;
     } else {
-        r.stage = (p0.flags & OF_FLAG_STAGE_I2) || t.stage_i2;
         r.fn = batch_kernel_for(p0.in_format, p0.storage, p0.radius);
-        r.smem = batch_smem_bytes(p0.radius, r.stage);
+        r.smem = batch_smem_bytes(p0.radius, false);
     }
     return r;
 }
@@ -370,6 +366,7 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
                 a.tiles = a.tiles_x * ((a.H + th - 1) / th);
                 a.status = bp[i].status;
                 a.stage_i2 = i1grad ? 0 : stage;
+                if (a.stage_i2) fill_stage_maps(a, I.m[i], level_elem(p0, l), p0.radius, tile_h);   // else gathered
                 a.hess = bp[i].hess;
                 a.hess_pitch = bp[i].pitch[l];
                 I.prefix[i + 1] = I.prefix[i] + a.tiles;
@@ -534,7 +531,7 @@ int batch_run_slot(BatchSlot &slot, int32_t n, const of_handle *hs, const void *
     }
     const Resolved rv = resolve(p0, t);
     BatchHdr hd;
-    fill_header(hd, p0, b, slot.dev, bar_off, rv.stage);
+    fill_header(hd, p0, b, slot.dev, bar_off);
     void *fn = rv.fn;
     const size_t smem = rv.smem;
     dim3 grid;
@@ -617,7 +614,7 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
             return OF_ECUDA;
         }
         const Resolved rv = resolve(p0, t);
-        fill_header(ne.hdr, p0, b, ne.dev, bar_off, rv.stage);
+        fill_header(ne.hdr, p0, b, ne.dev, bar_off);
         ne.fn = rv.fn;
         ne.smem = rv.smem;
         ne.phased = t.phased;

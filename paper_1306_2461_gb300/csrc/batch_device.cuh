@@ -36,7 +36,6 @@ struct BatchHdr {
     int32_t npairs, levels, iterations, radius, nphases, npyr;
     float fp64_cond;
     long long timeout_ns;
-    int32_t stage_i2;
     int32_t znssd;                      // phase 0 normalises the images (Eq. 2)
 };
 
@@ -194,9 +193,9 @@ __global__ void __launch_bounds__(LK_THREADS, batch_min_blocks<R>()) batch_kerne
                 a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
                 a.tiles = 0;
                 a.status = bp.status;
-                a.stage_i2 = hd.stage_i2;
-                if (l == 0 && !hd.znssd) live = lk_tile<Tin, false, R>(a, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
-                else live = lk_tile<T, false, R>(a, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
+                a.stage_i2 = 0;   // no tensor maps: the TMA staging needs them in parameter space
+                if (l == 0 && !hd.znssd) live = lk_tile<Tin, false, R>(a, nullptr, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
+                else live = lk_tile<T, false, R>(a, nullptr, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
             }
         }
         if (phase + 1 < hd.nphases && !grid_barrier(hd, (unsigned int)(phase + 1) * gridDim.x)) return;

@@ -1,17 +1,79 @@
 // Dispatch of the iteration, window-sum and batch kernels to their per-radius
 // instantiations (radius_<R>.cu): a specialised kernel for the radii listed in
 // OF_RADII, the generic one (radius at run time) for any other.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "of_internal.cuh"
 
 namespace of {
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+bool encode_tile_map(CUtensorMap *m, int elem, const void *base, int W, int H, size_t pitch_bytes, int box_w,
+                     int box_h)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base || W < 1 || H < 1 || box_w < 1 || box_h < 1 || box_w > 256 || box_h > 256) return false;
+    CUtensorMapDataType dt;
+    switch (elem) {
+    case ET_U8: dt = CU_TENSOR_MAP_DATA_TYPE_UINT8; break;
+    case ET_U16: dt = CU_TENSOR_MAP_DATA_TYPE_UINT16; break;
+    case ET_F32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    case ET_F16: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+    case ET_BF16: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+    case ET_FLOW2: dt = CU_TENSOR_MAP_DATA_TYPE_UINT64; break;
+    default: return false;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+#define OF_CASE_SMAP(R) \
+    case R: ok = radius_stage_maps<R>(a, m, elem, tile_h); break;
+bool fill_stage_maps(IterArgs &a, StageMaps &m, int elem, int radius, int tile_h)
+{
+    bool ok = false;
+    if (a.stage_i2) {
+        switch (radius) {
+            OF_RADII(OF_CASE_SMAP)
+        default: ok = false;
+        }
+    }
+    if (!ok) a.stage_i2 = 0;
+    return ok;
+}
+
 #define OF_CASE_LK(R) \
-    case R: return lk_launch<R>(a, elem, radius, fp64_cond, s);
-cudaError_t launch_lk_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s)
+    case R: return lk_launch<R>(a, m, elem, radius, fp64_cond, s);
+cudaError_t launch_lk_iter(const IterArgs &a, const StageMaps &m, int elem, int radius, float fp64_cond,
+                           cudaStream_t s)
 {
     switch (radius) {
         OF_RADII(OF_CASE_LK)
-    default: return lk_launch<0>(a, elem, radius, fp64_cond, s);
+    default: return lk_launch<0>(a, m, elem, radius, fp64_cond, s);
     }
 }
 

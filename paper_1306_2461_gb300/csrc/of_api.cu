@@ -215,13 +215,16 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
             const int th = i1grad ? I1_TH : LK_TH;   // the variant's kernels have their own tile height
             a.tiles = a.tiles_x * ((a.H + th - 1) / th);
             a.status = h->status;
-            a.stage_i2 = (p.flags & OF_FLAG_STAGE_I2) ? 1 : 0;
+            a.stage_i2 = (p.flags & OF_FLAG_STAGE_I2) && !i1grad ? 1 : 0;
+            StageMaps maps;
+            memset(&maps, 0, sizeof(maps));
+            if (a.stage_i2) fill_stage_maps(a, maps, level_elem(p, l), p.radius, LK_TH);   // else gathered
             if (i1grad) {
                 a.hess = h->hess;
                 a.hess_pitch = L.pitch[l];
                 e = launch_i1_iter(a, level_elem(p, l), p.radius, p.fp64_cond, st);
             } else {
-                e = launch_lk_iter(a, level_elem(p, l), p.radius, p.fp64_cond, st);
+                e = launch_lk_iter(a, maps, level_elem(p, l), p.radius, p.fp64_cond, st);
             }
             if (e != cudaSuccess) return e;
             cur = 1 - cur;

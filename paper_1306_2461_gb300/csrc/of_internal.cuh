@@ -1,6 +1,7 @@
 // Internal declarations of libof: storage types, level descriptors, kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -79,9 +80,17 @@ struct IterArgs {
     int32_t tiles_x;         // tiles along x (for flattened work lists)
     int32_t tiles;           // tiles in this level
     int *status;             // the handle's device status word (errors only)
-    int32_t stage_i2;        // stage the tile's I2 footprint in shared memory (fixed-radius tile)
+    int32_t stage_i2;        // stage the tile's I2 window (and, at FLOW_SAME, its estimate) in shared
+                             // memory with the TMA copies of the launch's StageMaps (fixed-radius tile)
     const float4 *hess;      // first-image-gradient variant: window matrix (Sa, Sb, Sc, 0) of this level
     int32_t hess_pitch;      // float4 elements per row of hess
+};
+
+// Tensor maps of the staged iteration tile, passed as kernel parameters (TMA reads them
+// from parameter space).
+struct StageMaps {
+    CUtensorMap flow;        // fin (8-byte elements, W x H) in boxes of the tile's region (FLOW_SAME)
+    CUtensorMap i2;          // I2 (storage type, W x H) in boxes of the tile's window
 };
 
 // Arguments of the per-level window-matrix pass of the first-image-gradient variant.
@@ -128,7 +137,9 @@ template <typename A> struct Phase {
     int32_t prefix[PHASE_PAIRS + 1];
     A a[PHASE_PAIRS];
 };
-using IterPhase = Phase<IterArgs>;
+struct IterPhase : Phase<IterArgs> {
+    StageMaps m[PHASE_PAIRS];           // pair p's tensor maps when a[p].stage_i2
+};
 using PyrPhase = Phase<PyrArgs>;
 using ZnPhase = Phase<ZnArgs>;
 using HessPhase = Phase<HessArgs>;
@@ -186,7 +197,8 @@ inline bool radius_specialised(int r)
 cudaError_t launch_pyr_first(const PyrArgs &a, int in_format, int storage, cudaStream_t s);
 cudaError_t launch_pyr_down(const PyrArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_znssd(const ZnArgs &a, int in_format, int storage, cudaStream_t s);
-cudaError_t launch_lk_iter(const IterArgs &a, int elem, int radius, float fp64_cond, cudaStream_t s);
+cudaError_t launch_lk_iter(const IterArgs &a, const StageMaps &m, int elem, int radius, float fp64_cond,
+                           cudaStream_t s);
 cudaError_t launch_window_sums(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
 // The variant linearised with the first image's gradient: window matrix of one level,
 // then iterations that read it from a.hess.
@@ -208,9 +220,22 @@ size_t batch_smem_generic(int radius);
 cudaError_t launch_level_to_f32(const Level &l, int elem, float *dst, cudaStream_t s);
 cudaError_t launch_wait_timeout(int *flag, int *status, long long timeout_ns, cudaStream_t s);
 cudaError_t configure_lk_kernels();   // all kernels with dynamic shared memory, current device
+// Fill a.tm_flow and a.tm_i2 for the staged fixed-radius tile of this radius and tile
+// height (level image type elem). Returns false (and clears a.stage_i2) when the radius
+// has no fixed-radius kernel or the tensor maps cannot be encoded; the tile then
+// gathers from global memory.
+bool fill_stage_maps(IterArgs &a, StageMaps &m, int elem, int radius, int tile_h);
+// Encode a 2-D tiled tensor map: W x H elements of elem_bytes with rows pitch_bytes apart,
+// boxes of box_w x box_h, zero fill outside. False if the driver entry point is missing or
+// the encoding fails.
+bool encode_tile_map(CUtensorMap *m, int elem, const void *base, int W, int H, size_t pitch_bytes, int box_w,
+                     int box_h);
+// Element type code for an 8-byte flow element in encode_tile_map.
+constexpr int ET_FLOW2 = 100;
 
 // Per-radius instantiations (radius_<R>.cu; R = 0 is the generic kernel).
-template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s);
+template <int R>
+cudaError_t lk_launch(const IterArgs &a, const StageMaps &m, int elem, int r, float fp64_cond, cudaStream_t s);
 template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, float *out, cudaStream_t s);
 template <int R> cudaError_t i1h_launch(const HessArgs &a, int elem, int r, cudaStream_t s);
 template <int R> cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, int tile_h, cudaStream_t s);
@@ -220,5 +245,6 @@ template <int R> cudaError_t i1_launch(const IterArgs &a, int elem, int r, float
 template <int R> void *batch_kernel_ptr(int in_format, int storage);
 template <int R> cudaError_t radius_configure();
 template <int R> size_t radius_smem_bytes(int r, bool stage_i2);
+template <int R> bool radius_stage_maps(const IterArgs &a, StageMaps &m, int elem, int tile_h);
 
 }  // namespace of

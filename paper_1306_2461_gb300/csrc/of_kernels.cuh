@@ -248,6 +248,21 @@ __device__ __forceinline__ float resid(float i1, float Iw, float gx, float gy, f
     return fmaf(gy, dy, fmaf(gx, dx, __fsub_rn(i1, Iw)));
 }
 
+// Packed FP32 pairs: sm_100 and later issue two FP32 additions, multiplications or fused
+// multiply-adds as one instruction, each component rounded exactly as the scalar
+// operation. The iteration tile runs its arithmetic on pairs of pixels (or of channels)
+// with these, so it computes the same bits as the scalar code with half the FP32
+// instructions. A difference a - b is formed as fma(b, -1, a), the same single rounding.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// lerpf on both components; omt = 1 - t
+__device__ __forceinline__ float2 lerp2(float2 p, float2 q, float2 t, float2 omt) { return fma2(t, q, mul2(omt, p)); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return add2(a, b); }
+
 // Bilinear sample with the position clamped to [0, W-1] x [0, H-1].
 template <bool NC, typename T>
 __device__ __forceinline__ float bil(const T *I, int pitch, int H, int W, float x, float y)
@@ -477,63 +492,55 @@ template <int R, int TH = LK_TH> struct FixedTile {
     static constexpr int PLANE = RH * RWP;
     static constexpr int NREG = RH * RW;               // region pixels
     static constexpr int PER = (NREG + LK_THREADS - 1) / LK_THREADS;   // region pixels per thread
-    // Staging of I2 (a.stage_i2): a window of the tile's region shifted by the tile's
-    // reference flow and widened by STAGE_MARGIN pixels (plus the 4x4 tap footprint and
-    // 16-byte alignment of its rows), in the storage type. WIN_BYTES holds it for 1- and
-    // 2-byte types; a larger window (FP32 storage) is not staged.
+    // Staging (a.stage_i2): one TMA box of I2, the window of the tile's region shifted by
+    // the tile's rounded reference flow and widened by STAGE_MARGIN pixels plus the 4x4
+    // tap footprint (and, for the alignment of its first column, E - 1 columns), in the
+    // storage type: WIN_W(S) x WIN_H elements of S bytes, rows WIN_W(S) elements apart.
+    // A pixel whose taps leave it reads them from global memory instead.
     static constexpr int STAGE_MARGIN = 6;
-    static constexpr int WIN_ROWS = TH + 2 * R + 2 * STAGE_MARGIN + 4;
-    static constexpr int WIN_BYTES = WIN_ROWS * 2 * (LK_TW + 2 * R + 2 * STAGE_MARGIN + 4 + 16);
-    static_assert(PLANE % 4 == 0, "the barrier and the window after the planes must be 16-byte aligned");
-    static constexpr int OFF_BAR = 5 * PLANE;       // 8-byte mbarrier
-    static constexpr int OFF_WIN = OFF_BAR + 4;     // 16-byte aligned staging window
-    static constexpr int SMEM_NOSTAGE = OFF_WIN;    // launches without I2 staging
-    static constexpr int SMEM_FLOATS = OFF_WIN + (WIN_BYTES + 15) / 16 * 4;
+    static constexpr int WIN_H = TH + 2 * R + 2 * STAGE_MARGIN + 4;
+    static constexpr int win_w(int S)
+    {
+        return (LK_TW + 2 * ((R + 1) / 2 * 2) + 2 * STAGE_MARGIN + 4 + 16 / S - 1 + 16 / S - 1) / (16 / S) * (16 / S);
+    }
+    static constexpr int win_bytes(int S) { return win_w(S) * WIN_H * S; }
+    // Product planes of the iteration tile. Stage 1 computes pixel pairs (x, x+1) with x
+    // even in image coordinates, so the region starts RE = R rounded up to even pixels
+    // left of the tile and is RWE columns wide; a window's first column is then OFF =
+    // RE - R columns into the region. Channels 0 and 1 share one plane of float2 (P01),
+    // channels 2 and 3 another (P23), channel 4 has a plane of floats (P4), so that the
+    // box sums add two channels per instruction. Row lengths: RWP1 floats for P4 (a
+    // multiple of 4), RWP2 float2 for the pair planes (2 mod 4, so that the float4 reads
+    // of a quarter warp of the horizontal pass fall in distinct banks).
+    static constexpr int RE = (R + 1) / 2 * 2;
+    static constexpr int OFF = RE - R;
+    static constexpr int RWE = LK_TW + 2 * RE;
+    static constexpr int NVE = (OFF + 2 * R + 4 + 3) / 4;   // float4 column groups read per 4 outputs
+    static_assert(LK_TW - 4 + 4 * NVE <= RWE, "the horizontal pass reads computed columns only");
+    static constexpr int RWP1 = RWE;
+    static constexpr int RWP2 = RWE + 2;
+    static_assert(RWP1 % 4 == 0 && RWP2 % 4 == 2, "row lengths");
+    static constexpr int PAIR_PLANE = RH * RWP2;             // float2 per pair plane
+    static constexpr int PLANES = 4 * PAIR_PLANE + RH * RWP1;  // floats of the three planes
+    static_assert(PLANES % 4 == 0, "the barrier after the planes must be 8-byte aligned");
+    static constexpr int OFF_BAR = PLANES;                    // 8-byte mbarrier
+    static constexpr int OFF_WIN = (OFF_BAR + 2 + 31) / 32 * 32;   // 128-byte aligned staging window
+    static constexpr int SMEM_NOSTAGE = OFF_WIN;              // launches without staging
+    static constexpr int smem_staged(int S) { return OFF_WIN + (win_bytes(S) + 15) / 16 * 4; }
+    static constexpr int SMEM_FLOATS = smem_staged(4);        // the largest (FP32 storage)
+    // the staged flow estimate is one TMA box of RWP2 x RH 8-byte elements written over P01
+    static constexpr int FLOW_BOX_BYTES = RWP2 * RH * 8;
 #ifndef OF_LK_MIN_BLOCKS
-#define OF_LK_MIN_BLOCKS 5   // resident blocks per SM the fixed-radius kernels are compiled for (R <= 6)
+#define OF_LK_MIN_BLOCKS 4   // resident blocks per SM the fixed-radius kernels are compiled for (R <= 6)
 #endif
     // resident blocks per SM the kernels are compiled for: the measured choice for the
     // default tile height, else as many as the shared memory holds (at most 5)
-    static constexpr int SMEM_FIT = 233472 / (4 * (5 * PLANE + 4) + 1024);
+    static constexpr int SMEM_FIT = 233472 / (4 * (PLANES + 4) + 1024);
     static constexpr int MIN_BLOCKS =
         TH == LK_TH ? (R <= 6 ? OF_LK_MIN_BLOCKS : 2) : (SMEM_FIT < 1 ? 1 : (SMEM_FIT > 5 ? 5 : SMEM_FIT));
 };
 
-constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's row copies
-
-template <typename T> __device__ __forceinline__ float ld_smem_elem(const unsigned char *p)
-{
-    return ldf<false>(reinterpret_cast<const T *>(p));
-}
-
-// The interior branch of sample_grad with its 12 taps read from the staged window (rows
-// wy0.., columns wx0.., `rowbytes` per row). Returns false, reading nothing, when the
-// 4x4 footprint of (px, py) is not inside both the window and the image's interior.
-template <typename T>
-__device__ __forceinline__ bool sample_grad_win(const unsigned char *win, int rowbytes, int wx0, int wy0, int wx1,
-                                                int wy1, int H, int W, float px, float py, float &Iw, float &gx,
-                                                float &gy)
-{
-    if (!(px >= 1.0f && py >= 1.0f && px < (float)(W - 2) && py < (float)(H - 2))) return false;
-    const float fx = floorf(px), fy = floorf(py);
-    const int x0 = (int)fx, y0 = (int)fy;
-    if (x0 - 1 < wx0 || x0 + 2 >= wx1 || y0 - 1 < wy0 || y0 + 2 >= wy1) return false;
-    const float ax = px - fx, ay = py - fy;
-    constexpr int S = (int)sizeof(T);
-    const unsigned char *rm = win + (y0 - 1 - wy0) * rowbytes + (x0 - wx0) * S;
-    const unsigned char *r0 = rm + rowbytes, *r1 = r0 + rowbytes, *r2 = r1 + rowbytes;
-    const float a0 = ld_smem_elem<T>(rm), a1 = ld_smem_elem<T>(rm + S);
-    const float bm = ld_smem_elem<T>(r0 - S), b0 = ld_smem_elem<T>(r0), b1 = ld_smem_elem<T>(r0 + S),
-                b2 = ld_smem_elem<T>(r0 + 2 * S);
-    const float cm = ld_smem_elem<T>(r1 - S), c0 = ld_smem_elem<T>(r1), c1 = ld_smem_elem<T>(r1 + S),
-                c2 = ld_smem_elem<T>(r1 + 2 * S);
-    const float d0 = ld_smem_elem<T>(r2), d1 = ld_smem_elem<T>(r2 + S);
-    const float top = lerpf(b0, b1, ax), bot = lerpf(c0, c1, ax);
-    Iw = lerpf(top, bot, ay);
-    gx = (lerpf(lerpf(b1, b2, ax), lerpf(c1, c2, ax), ay) - lerpf(lerpf(bm, b0, ax), lerpf(cm, c0, ax), ay)) * 0.5f;
-    gy = (lerpf(bot, lerpf(d0, d1, ax), ay) - lerpf(lerpf(a0, a1, ax), top, ay)) * 0.5f;
-    return true;
-}
+constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's staging copies
 
 // o[j] = sum_{k=0}^{2R} v[j+k], j = 0..3, from v[0 .. 2R+3].
 template <int R>
@@ -612,6 +619,287 @@ __device__ __forceinline__ void box_v4(const float *P, int g, int tx, float s[C]
     }
 }
 
+// --------------------------------------------------- pixel-pair and channel-pair passes
+// Two horizontally adjacent pixels (x even) of a level image, as floats (exact for every
+// storage type; the second is 0 when q is false, and then only the first is read).
+template <bool NC> __device__ __forceinline__ float2 ld_pair(const uint8_t *p, bool q)
+{
+    if (!q) return f2(ldf<NC>(p), 0.0f);
+    const uchar2 w = ld<NC>(reinterpret_cast<const uchar2 *>(p));
+    return f2((float)w.x, (float)w.y);
+}
+template <bool NC> __device__ __forceinline__ float2 ld_pair(const uint16_t *p, bool q)
+{
+    if (!q) return f2(ldf<NC>(p), 0.0f);
+    const ushort2 w = ld<NC>(reinterpret_cast<const ushort2 *>(p));
+    return f2((float)w.x, (float)w.y);
+}
+template <bool NC> __device__ __forceinline__ float2 ld_pair(const float *p, bool q)
+{
+    if (!q) return f2(ldf<NC>(p), 0.0f);
+    return ld<NC>(reinterpret_cast<const float2 *>(p));
+}
+template <bool NC> __device__ __forceinline__ float2 ld_pair(const __half *p, bool q)
+{
+    if (!q) return f2(ldf<NC>(p), 0.0f);
+    const __half2 w = ld<NC>(reinterpret_cast<const __half2 *>(p));
+    return __half22float2(w);
+}
+template <bool NC> __device__ __forceinline__ float2 ld_pair(const __nv_bfloat16 *p, bool q)
+{
+    if (!q) return f2(ldf<NC>(p), 0.0f);
+    const __nv_bfloat162 w = ld<NC>(reinterpret_cast<const __nv_bfloat162 *>(p));
+    return __bfloat1622float2(w);
+}
+
+// The current estimates of the pixel pair (x, y), (x + 1, y) (x even; the second only
+// when q): one 16-byte load of the same-level flow, else pixel by pixel.
+template <bool NC, int MODE>
+__device__ __forceinline__ void flow_pair(const IterArgs &a, int x, int y, bool q, float2 &fp, float2 &fq)
+{
+    if (MODE == FLOW_SAME || (MODE < 0 && a.mode == FLOW_SAME)) {
+        if (q) {
+            const float4 w = ld<NC>(reinterpret_cast<const float4 *>(a.fin + (y * a.fin_pitch + x)));
+            fp = f2(w.x, w.y);
+            fq = f2(w.z, w.w);
+            return;
+        }
+    }
+    fp = flow_mode<NC, MODE>(a, x, y);
+    fq = q ? flow_mode<NC, MODE>(a, x + 1, y) : f2(0.0f, 0.0f);
+}
+
+__device__ __forceinline__ bool interior(float px, float py, int H, int W)
+{
+    return px >= 1.0f && py >= 1.0f && px < (float)(W - 2) && py < (float)(H - 2);
+}
+
+// The interior branch of sample_grad for two sample positions at once (X, Y: their
+// coordinates), with every operation of the scalar form on both components. The 12 taps
+// of each come from the staged window (win: WW x WH elements, first element at image
+// (wx0, wy0)) when both 4x4 footprints lie inside it, else from global memory.
+template <bool NC, int WW, typename T>
+__device__ __forceinline__ void sample_grad2(const T *I, int pitch, const T *win, int wx0, int wy0, int WH, float2 X,
+                                             float2 Y, float2 &IW, float2 &GX, float2 &GY)
+{
+    const float2 FX = f2(floorf(X.x), floorf(X.y)), FY = f2(floorf(Y.x), floorf(Y.y));
+    const float2 AX = sub2(X, FX), AY = sub2(Y, FY);
+    const float2 one = f2(1.0f, 1.0f);
+    const float2 OX = sub2(one, AX), OY = sub2(one, AY);
+    const int xp = (int)FX.x, yp = (int)FY.x, xq = (int)FX.y, yq = (int)FY.y;
+    float2 A0, A1, BM, B0, B1, B2, CM, C0, C1, C2, D0, D1;
+    if (win && xp - 1 >= wx0 && xq - 1 >= wx0 && xp + 2 < wx0 + WW && xq + 2 < wx0 + WW && yp - 1 >= wy0 &&
+        yq - 1 >= wy0 && yp + 2 < wy0 + WH && yq + 2 < wy0 + WH) {
+        // rows WW elements apart: every tap at a constant offset from the pixel's corner
+        const T *p = win + ((yp - 1 - wy0) * WW + (xp - wx0)), *q = win + ((yq - 1 - wy0) * WW + (xq - wx0));
+        A0 = f2(ldf<false>(p), ldf<false>(q));
+        A1 = f2(ldf<false>(p + 1), ldf<false>(q + 1));
+        BM = f2(ldf<false>(p + WW - 1), ldf<false>(q + WW - 1));
+        B0 = f2(ldf<false>(p + WW), ldf<false>(q + WW));
+        B1 = f2(ldf<false>(p + WW + 1), ldf<false>(q + WW + 1));
+        B2 = f2(ldf<false>(p + WW + 2), ldf<false>(q + WW + 2));
+        CM = f2(ldf<false>(p + 2 * WW - 1), ldf<false>(q + 2 * WW - 1));
+        C0 = f2(ldf<false>(p + 2 * WW), ldf<false>(q + 2 * WW));
+        C1 = f2(ldf<false>(p + 2 * WW + 1), ldf<false>(q + 2 * WW + 1));
+        C2 = f2(ldf<false>(p + 2 * WW + 2), ldf<false>(q + 2 * WW + 2));
+        D0 = f2(ldf<false>(p + 3 * WW), ldf<false>(q + 3 * WW));
+        D1 = f2(ldf<false>(p + 3 * WW + 1), ldf<false>(q + 3 * WW + 1));
+    } else {
+        const int op = (yp - 1) * pitch + xp, oq = (yq - 1) * pitch + xq;
+        const T *mp = I + op, *mq = I + oq;
+        const T *p0 = I + (op + pitch), *q0 = I + (oq + pitch);
+        const T *p1 = I + (op + 2 * pitch), *q1 = I + (oq + 2 * pitch);
+        const T *p2 = I + (op + 3 * pitch), *q2 = I + (oq + 3 * pitch);
+        A0 = f2(ldf<NC>(mp), ldf<NC>(mq));
+        A1 = f2(ldf<NC>(mp + 1), ldf<NC>(mq + 1));
+        BM = f2(ldf<NC>(p0 - 1), ldf<NC>(q0 - 1));
+        B0 = f2(ldf<NC>(p0), ldf<NC>(q0));
+        B1 = f2(ldf<NC>(p0 + 1), ldf<NC>(q0 + 1));
+        B2 = f2(ldf<NC>(p0 + 2), ldf<NC>(q0 + 2));
+        CM = f2(ldf<NC>(p1 - 1), ldf<NC>(q1 - 1));
+        C0 = f2(ldf<NC>(p1), ldf<NC>(q1));
+        C1 = f2(ldf<NC>(p1 + 1), ldf<NC>(q1 + 1));
+        C2 = f2(ldf<NC>(p1 + 2), ldf<NC>(q1 + 2));
+        D0 = f2(ldf<NC>(p2), ldf<NC>(q2));
+        D1 = f2(ldf<NC>(p2 + 1), ldf<NC>(q2 + 1));
+    }
+    const float2 TOP = lerp2(B0, B1, AX, OX), BOT = lerp2(C0, C1, AX, OX);
+    IW = lerp2(TOP, BOT, AY, OY);
+    const float2 half = f2(0.5f, 0.5f);
+    GX = mul2(sub2(lerp2(lerp2(B1, B2, AX, OX), lerp2(C1, C2, AX, OX), AY, OY),
+                   lerp2(lerp2(BM, B0, AX, OX), lerp2(CM, C0, AX, OX), AY, OY)),
+              half);
+    GY = mul2(sub2(lerp2(BOT, lerp2(D0, D1, AX, OX), AY, OY), lerp2(lerp2(A0, A1, AX, OX), TOP, AY, OY)), half);
+}
+
+// o[j] = sum_{k=0}^{2R} v[OFF+j+k], j = 0..3, the additions in box4's order (floats or
+// float2 pairs of channels).
+template <int R, int OFF, typename V>
+__device__ __forceinline__ void box4v(const V *v, V o[4])
+{
+    V m = v[OFF + 3];
+#pragma unroll
+    for (int k = 4; k <= 2 * R; ++k) m = vadd(m, v[OFF + k]);
+    o[0] = vadd(vadd(vadd(v[OFF], v[OFF + 1]), v[OFF + 2]), m);
+    o[1] = vadd(vadd(vadd(v[OFF + 1], v[OFF + 2]), m), v[OFF + 2 * R + 1]);
+    o[2] = vadd(vadd(vadd(v[OFF + 2], m), v[OFF + 2 * R + 1]), v[OFF + 2 * R + 2]);
+    o[3] = vadd(vadd(vadd(m, v[OFF + 2 * R + 1]), v[OFF + 2 * R + 2]), v[OFF + 2 * R + 3]);
+}
+
+// Horizontal pass of one pair plane, in place: row ry becomes, at columns 0..LK_TW-1,
+// the window sums of its outputs (two channels per float2). A warp takes two rows; a
+// quarter warp takes 4 groups of 4 outputs of each (with rows RWP2 = 2 mod 4 float2
+// long, its 16-byte reads hit distinct banks). Each row is read and rewritten by one warp.
+template <int R, int TH>
+__device__ __forceinline__ void box_h_pairs(float2 *P)
+{
+    using F = FixedTile<R, TH>;
+    static_assert(LK_TW == 64 && LK_THREADS % 32 == 0, "a warp covers two rows of 16 groups");
+    constexpr int ROWP = F::RH / 2;
+    constexpr int WARPS = LK_THREADS / 32;
+    constexpr int RW4 = F::RWP2 / 2;   // float4 per row
+    const int lane = threadIdx.x & 31;
+    const int rsub = (lane >> 2) & 1, g = ((lane >> 3) << 2) | (lane & 3);
+#pragma unroll 1
+    for (int chunk = threadIdx.x >> 5; chunk < ROWP; chunk += WARPS) {
+        float4 *row = reinterpret_cast<float4 *>(P) + (2 * chunk + rsub) * RW4 + 2 * g;
+        float2 v[4 * F::NVE];
+#pragma unroll
+        for (int q = 0; q < 2 * F::NVE; ++q) {
+            const float4 t = row[q];
+            v[2 * q] = f2(t.x, t.y);
+            v[2 * q + 1] = f2(t.z, t.w);
+        }
+        float2 o[4];
+        box4v<R, F::OFF>(v, o);
+        __syncwarp();
+        row[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+        row[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+    }
+}
+
+// Horizontal pass of the float plane P4, in place (16 items of a row in 16 lanes).
+template <int R, int TH>
+__device__ __forceinline__ void box_h_single(float *P)
+{
+    using F = FixedTile<R, TH>;
+    constexpr int NG = LK_TW / 4;
+    constexpr int NITEMS = F::RH * NG;
+    constexpr int IT = (NITEMS + LK_THREADS - 1) / LK_THREADS;
+    float4 res[IT];
+#pragma unroll
+    for (int k = 0; k < IT; ++k) {
+        const int i = threadIdx.x + k * LK_THREADS;
+        if (i < NITEMS) {
+            const int ry = i / NG, g = i % NG;
+            const float4 *src = reinterpret_cast<const float4 *>(P + ry * F::RWP1 + 4 * g);
+            float v[4 * F::NVE];
+#pragma unroll
+            for (int q = 0; q < F::NVE; ++q) {
+                const float4 t = src[q];
+                v[4 * q] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+            float o[4];
+            box4v<R, F::OFF>(v, o);
+            res[k] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < IT; ++k) {
+        const int i = threadIdx.x + k * LK_THREADS;
+        if (i < NITEMS) {
+            const int ry = i / NG, g = i % NG;
+            *reinterpret_cast<float4 *>(P + ry * F::RWP1 + 4 * g) = res[k];
+        }
+    }
+}
+
+// Vertical pass for the 4 outputs (rows 4g..4g+3, column tx): sums of the three planes.
+template <int R, int TH>
+__device__ __forceinline__ void box_v_planes(const float2 *P01, const float2 *P23, const float *P4, int g, int tx,
+                                             float2 s01[4], float2 s23[4], float s4[4])
+{
+    using F = FixedTile<R, TH>;
+    {
+        float2 v[2 * R + 4];
+#pragma unroll
+        for (int q = 0; q < 2 * R + 4; ++q) v[q] = P01[(4 * g + q) * F::RWP2 + tx];
+        box4v<R, 0>(v, s01);
+    }
+    {
+        float2 v[2 * R + 4];
+#pragma unroll
+        for (int q = 0; q < 2 * R + 4; ++q) v[q] = P23[(4 * g + q) * F::RWP2 + tx];
+        box4v<R, 0>(v, s23);
+    }
+    {
+        float v[2 * R + 4];
+#pragma unroll
+        for (int q = 0; q < 2 * R + 4; ++q) v[q] = P4[(4 * g + q) * F::RWP1 + tx];
+        box4v<R, 0>(v, s4);
+    }
+}
+
+// Stage 1 of the fixed-radius tile for the pixel pair (x, y), (x + 1, y): warp I2 by the
+// current estimate, its gradient there, e~ and the five products, on both pixels at
+// once when both sample the interior (taps from the staged window or global memory),
+// pixel by pixel near the border or at the image's last column. sflow: the pair's staged
+// estimates (NULL: read them from fin). Out-of-image pixels get zero products. Returns the
+// products in the planes' layout.
+template <typename T, bool NC, int MODE, int WW>
+__device__ __forceinline__ void stage1_pair(const IterArgs &a, int x, int y, float2 ref, const float4 *sflow,
+                                            const T *win, int wx0, int wy0, int WH, float4 &s01, float4 &s23,
+                                            float2 &s4)
+{
+    s01 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    s23 = s01;
+    s4 = f2(0.0f, 0.0f);
+    const bool rowin = (unsigned)y < (unsigned)a.H;
+    const bool inp = rowin && (unsigned)x < (unsigned)a.W;
+    const bool inq = rowin && (unsigned)(x + 1) < (unsigned)a.W;   // implies inp (x even)
+    if (!inp) return;
+    const T *I1 = static_cast<const T *>(a.I1);
+    const T *I2 = static_cast<const T *>(a.I2);
+    float2 fp, fq;
+    if (sflow) {
+        const float4 w = *sflow;   // zeros beyond the image
+        fp = f2(w.x, w.y);
+        fq = f2(w.z, w.w);
+    } else {
+        flow_pair<NC, MODE>(a, x, y, inq, fp, fq);
+    }
+    const float2 i1 = ld_pair<NC>(I1 + (y * a.pitch + x), inq);
+    const float2 X = add2(f2((float)x, (float)(x + 1)), f2(fp.x, fq.x));
+    const float2 Y = add2(f2((float)y, (float)y), f2(fp.y, fq.y));
+    float2 IW, GX, GY;
+    if (inq && interior(X.x, Y.x, a.H, a.W) && interior(X.y, Y.y, a.H, a.W)) {
+        sample_grad2<NC, WW>(I2, a.pitch, win, wx0, wy0, WH, X, Y, IW, GX, GY);
+    } else {
+        float iw0, gx0, gy0, iw1 = 0.0f, gx1 = 0.0f, gy1 = 0.0f;
+        sample_grad<NC>(I2, a.pitch, a.H, a.W, X.x, Y.x, iw0, gx0, gy0);
+        if (inq) sample_grad<NC>(I2, a.pitch, a.H, a.W, X.y, Y.y, iw1, gx1, gy1);
+        IW = f2(iw0, iw1);
+        GX = f2(gx0, gx1);
+        GY = f2(gy0, gy1);
+    }
+    const float2 DX = sub2(f2(fp.x, fq.x), f2(ref.x, ref.x)), DY = sub2(f2(fp.y, fq.y), f2(ref.y, ref.y));
+    const float2 E = fma2(GY, DY, fma2(GX, DX, sub2(i1, IW)));
+    const float2 q0 = mul2(GX, GX), q1 = mul2(GX, GY), q2 = mul2(GY, GY), q3 = mul2(GX, E), q4 = mul2(GY, E);
+    if (inq) {
+        s01 = make_float4(q0.x, q1.x, q0.y, q1.y);
+        s23 = make_float4(q2.x, q3.x, q2.y, q3.y);
+        s4 = q4;
+    } else {
+        s01 = make_float4(q0.x, q1.x, 0.0f, 0.0f);
+        s23 = make_float4(q2.x, q3.x, 0.0f, 0.0f);
+        s4 = f2(q4.x, 0.0f);
+    }
+}
+
 // The tile's mbarrier: initialised once per block, before the first tile.
 template <int R, int TH = LK_TH> __device__ __forceinline__ void lk_tile_init(float *smem)
 {
@@ -625,98 +913,72 @@ template <int R, int TH = LK_TH> __device__ __forceinline__ void lk_tile_init(fl
 // Returns false if the staging copy did not complete in time (then OF_ETIMEOUT is in
 // *a.status, nothing of the tile was written, and the block must stop).
 template <typename T, bool NC, int R, int MODE, int TH = LK_TH>
-__device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float fp64_cond, float *smem,
-                                              uint32_t &phase)
+__device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps *maps, int tile, float fp64_cond,
+                                              float *smem, uint32_t &phase)
 {
     using F = FixedTile<R, TH>;
-    float *P = smem;
     unsigned char *win = reinterpret_cast<unsigned char *>(smem + F::OFF_WIN);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + F::OFF_BAR);
     const int tyi = tile / a.tiles_x;
     const int ty0 = tyi * TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
     const float2 ref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + TH / 2, a.H - 1));
-    const T *I1 = static_cast<const T *>(a.I1);
-    const T *I2 = static_cast<const T *>(a.I2);
     __syncthreads();   // the previous tile's readers of smem are done
-    // Staging: the window of I2 around the tile's region displaced by the reference flow,
-    // row by row with bulk copies (raw storage type, 16-byte aligned rows, clamped to the
-    // image's rows and to the padded row length). The window is the same for every thread.
-    int wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0, rowbytes = 0;
-    bool staged = false;
-    if (a.stage_i2) {
-        constexpr int E = 16 / (int)sizeof(T);   // elements per 16-byte chunk
+    // Staging (a.stage_i2): one TMA box of I2, the tile's window displaced by the rounded
+    // reference flow, and at FLOW_SAME one box of the current estimate over the tile's
+    // region, written over plane P01: stage 1 reads each pair's estimate there before
+    // storing the pair's products in the same place.
+    constexpr int S = (int)sizeof(T);
+    constexpr int WW = F::win_w(S);
+    constexpr bool SAME = MODE == FLOW_SAME;
+    float2 *P01 = reinterpret_cast<float2 *>(smem);
+    float2 *P23 = P01 + F::PAIR_PLANE;
+    float *P4 = reinterpret_cast<float *>(P23 + F::PAIR_PLANE);
+    const bool staged = maps && a.stage_i2 != 0;
+    int wx0 = 0, wy0 = 0;
+    if (staged) {
+        constexpr int E = 16 / S;
         const int ox = __float2int_rn(fminf(fmaxf(ref.x, -(float)a.W), (float)a.W));
         const int oy = __float2int_rn(fminf(fmaxf(ref.y, -(float)a.H), (float)a.H));
-        wx0 = max(tx0 - R - F::STAGE_MARGIN + ox - 1, 0) / E * E;
-        wx1 = (min(tx0 + LK_TW + R + F::STAGE_MARGIN + ox + 3, a.pitch) + E - 1) / E * E;   // pitch: multiple of E
-        wy0 = max(ty0 - R - F::STAGE_MARGIN + oy - 1, 0);
-        wy1 = min(ty0 + TH + R + F::STAGE_MARGIN + oy + 3, a.H);
-        rowbytes = (wx1 - wx0) * (int)sizeof(T);
-        const int rows = wy1 - wy0;
-        staged = wx1 > wx0 && rows > 0 && rows * rowbytes <= F::WIN_BYTES;
-        if (staged) {
-            if (threadIdx.x < 32) {
-                if (threadIdx.x == 0) {
-                    fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(bar, (uint32_t)(rows * rowbytes));
-                }
-                __syncwarp();
-                fence_proxy_async_global();
-                for (int k = threadIdx.x; k < rows; k += 32)
-                    bulk_g2s(win + k * rowbytes, I2 + (size_t)(wy0 + k) * a.pitch + wx0, (uint32_t)rowbytes, bar);
-            }
-            const bool done = mbar_wait_bounded(bar, phase, STAGE_TIMEOUT_NS);
-            phase ^= 1u;
-            if (__syncthreads_or(!done)) {
-                if (threadIdx.x == 0 && a.status) atomicExch(a.status, DEV_TIMEOUT);
-                return false;
-            }
+        const int wx = tx0 - F::RE + ox - F::STAGE_MARGIN - 2;
+        wx0 = (wx >= 0 ? wx / E : -((-wx + E - 1) / E)) * E;   // a multiple of 16 bytes
+        wy0 = ty0 - R + oy - F::STAGE_MARGIN - 2;
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, (uint32_t)(F::win_bytes(S) + (SAME ? F::FLOW_BOX_BYTES : 0)));
+            if (SAME) tma_load_2d(P01, &maps->flow, tx0 - F::RE, ty0 - R, bar);
+            tma_load_2d(win, &maps->i2, wx0, wy0, bar);
         }
+        bool done = mbar_wait_bounded(bar, phase, STAGE_TIMEOUT_NS);
+        if (__syncthreads_or(!done)) {
+            // give the copies in flight a further bounded wait before the block leaves
+            if (!done) mbar_wait_bounded(bar, phase, STAGE_TIMEOUT_NS);
+            if (threadIdx.x == 0 && a.status) atomicExch(a.status, DEV_TIMEOUT);
+            return false;
+        }
+        phase ^= 1u;
     }
-    // stage 1: products over the tile and its R-pixel halo. The current estimates of
-    // S1 pixels are loaded before any of them is used, so that their latencies overlap.
-    constexpr int S1 = 3;   // measured: 1, 2, 3, 4, 6, 12 -> 3 is fastest
+    // stage 1: products over the tile and its halo, by pixel pairs
+    constexpr int NPR = F::RWE / 2;   // pairs per region row
+    constexpr int NPAIR = F::RH * NPR;
+    const T *wt = staged ? reinterpret_cast<const T *>(win) : nullptr;
 #pragma unroll 1
-    for (int k0 = 0; k0 < F::PER; k0 += S1) {
-        float2 f[S1];
-        bool in[S1];
-#pragma unroll
-        for (int u = 0; u < S1; ++u) {
-            const int i = threadIdx.x + (k0 + u) * LK_THREADS;
-            const int ry = i / F::RW, rx = i - ry * F::RW;
-            const int y = ty0 - R + ry, x = tx0 - R + rx;
-            in[u] = i < F::NREG && (unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W;
-            f[u] = in[u] ? flow_mode<NC, MODE>(a, x, y) : make_float2(0.0f, 0.0f);
-        }
-#pragma unroll
-        for (int u = 0; u < S1; ++u) {
-            const int i = threadIdx.x + (k0 + u) * LK_THREADS;
-            if (i >= F::NREG) break;
-            const int ry = i / F::RW, rx = i - ry * F::RW;
-            const int y = ty0 - R + ry, x = tx0 - R + rx;
-            float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f, p4 = 0.0f;
-            if (in[u]) {
-                float Iw, gx, gy;
-                const float px = (float)x + f[u].x, py = (float)y + f[u].y;
-                if (!(staged && sample_grad_win<T>(win, rowbytes, wx0, wy0, wx1, wy1, a.H, a.W, px, py, Iw, gx, gy)))
-                    sample_grad<NC>(I2, a.pitch, a.H, a.W, px, py, Iw, gx, gy);
-                const float e = resid(ldf<NC>(I1 + (y * a.pitch + x)), Iw, gx, gy, f[u].x - ref.x, f[u].y - ref.y);
-                p0 = gx * gx;
-                p1 = gx * gy;
-                p2 = gy * gy;
-                p3 = gx * e;
-                p4 = gy * e;
-            }
-            float *q = P + ry * F::RWP + rx;
-            q[0] = p0;
-            q[F::PLANE] = p1;
-            q[2 * F::PLANE] = p2;
-            q[3 * F::PLANE] = p3;
-            q[4 * F::PLANE] = p4;
-        }
+    for (int j = threadIdx.x; j < NPAIR; j += LK_THREADS) {
+        const int ry = j / NPR, cx = j - ry * NPR;
+        const int k2 = ry * (F::RWP2 / 2) + cx;   // float4 slot of the pair in the pair planes
+        float4 s01, s23;
+        float2 s4;
+        stage1_pair<T, NC, MODE, WW>(a, tx0 - F::RE + 2 * cx, ty0 - R + ry, ref,
+                                     (SAME && staged) ? reinterpret_cast<const float4 *>(P01) + k2 : nullptr, wt, wx0,
+                                     wy0, F::WIN_H, s01, s23, s4);
+        reinterpret_cast<float4 *>(P01)[k2] = s01;
+        reinterpret_cast<float4 *>(P23)[k2] = s23;
+        reinterpret_cast<float2 *>(P4)[ry * (F::RWP1 / 2) + cx] = s4;
     }
     __syncthreads();
-    box_h_inplace<R, 5, TH>(P);
+    box_h_pairs<R, TH>(P01);
+    box_h_pairs<R, TH>(P23);
+    box_h_single<R, TH>(P4);
+    __syncthreads();
     // vertical sums, solve and write, 4 rows of one column per item
     constexpr int VITEMS = LK_TW * (TH / 4);
 #pragma unroll 1
@@ -724,13 +986,14 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
         const int tx = i % LK_TW, g = i / LK_TW;
         const int x = tx0 + tx;
         if (x >= a.W || ty0 + 4 * g >= a.H) continue;
-        float s[5][4];
-        box_v4<R, 5, TH>(P, g, tx, s);
+        float2 s01[4], s23[4];
+        float s4[4];
+        box_v_planes<R, TH>(P01, P23, P4, g, tx, s01, s23, s4);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int y = ty0 + 4 * g + j;
             if (y >= a.H) break;
-            const float sj[5] = {s[0][j], s[1][j], s[2][j], s[3][j], s[4][j]};
+            const float sj[5] = {s01[j].x, s01[j].y, s23[j].x, s23[j].y, s4[j]};
             float xu, xv;
             const float2 f = solve2(sj, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv) : flow_mode<NC, MODE>(a, x, y);
             if (a.fout) {
@@ -745,17 +1008,18 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, int tile, float
 }
 
 // The iteration tile for radius R (0 = generic, radius r at run time). MODE: the flow
-// mode when it is known at compile time (-1: read a.mode at run time). Returns false
-// when the block must stop (a staging copy timed out; recorded in *a.status).
+// mode when it is known at compile time (-1: read a.mode at run time). maps: the staging
+// tensor maps in parameter space (NULL: gather from global memory). Returns false when
+// the block must stop (a staging copy timed out; recorded in *a.status).
 template <typename T, bool NC, int R, int MODE = -1, int TH = LK_TH>
-__device__ __forceinline__ bool lk_tile(const IterArgs &a, int tile, int r, float fp64_cond, float *smem,
-                                        uint32_t &phase)
+__device__ __forceinline__ bool lk_tile(const IterArgs &a, const StageMaps *maps, int tile, int r, float fp64_cond,
+                                        float *smem, uint32_t &phase)
 {
     if constexpr (R == 0) {
         lk_tile_generic<T, NC>(a, tile, r, fp64_cond, smem);
         return true;
     } else {
-        return lk_tile_fixed<T, NC, R, MODE, TH>(a, tile, fp64_cond, smem, phase);
+        return lk_tile_fixed<T, NC, R, MODE, TH>(a, maps, tile, fp64_cond, smem, phase);
     }
 }
 
@@ -780,10 +1044,13 @@ template <int R> constexpr int batch_min_blocks()
     return m < OF_BATCH_MIN_BLOCKS ? m : OF_BATCH_MIN_BLOCKS;
 }
 
-template <int R, int TH = LK_TH> inline __host__ __device__ int lk_tile_smem_floats(int r, bool stage_i2)
+// Dynamic shared memory of the iteration tile (floats); elem_bytes: the level image's
+// element size (the staged window's).
+template <int R, int TH = LK_TH>
+inline __host__ __device__ int lk_tile_smem_floats(int r, bool stage_i2, int elem_bytes = 4)
 {
     if constexpr (R == 0) return lk_smem_floats(r);
-    else return stage_i2 ? FixedTile<R, TH>::SMEM_FLOATS : FixedTile<R, TH>::SMEM_NOSTAGE;
+    else return stage_i2 ? FixedTile<R, TH>::smem_staged(elem_bytes) : FixedTile<R, TH>::SMEM_NOSTAGE;
 }
 
 }  // namespace of

@@ -14,13 +14,14 @@
 namespace of {
 
 template <typename T, int R>
-__global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>()) lk_iter_kernel(IterArgs a, int r, float fp64_cond)
+__global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R>())
+lk_iter_kernel(const __grid_constant__ IterArgs a, const __grid_constant__ StageMaps m, int r, float fp64_cond)
 {
-    extern __shared__ float4 smem4[];
+    extern __shared__ __align__(128) float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
     uint32_t phase = 0;
     lk_tile_prepare<R>(smem);
-    lk_tile<T, true, R>(a, blockIdx.x, r, fp64_cond, smem, phase);
+    lk_tile<T, true, R>(a, &m, blockIdx.x, r, fp64_cond, smem, phase);
 }
 
 // One iteration of up to PHASE_PAIRS pairs on one level: block b runs tile
@@ -29,7 +30,7 @@ template <typename T, int R, int MODE, int TH>
 __global__ void __launch_bounds__(LK_THREADS, lk_min_blocks<R, TH>())
 phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
 {
-    extern __shared__ float4 smem4[];
+    extern __shared__ __align__(128) float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
     if constexpr (R != 0) {
         const int t2 = blockIdx.x + P.ahead;
@@ -41,7 +42,7 @@ phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
     const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
     uint32_t phase = 0;
     lk_tile_prepare<R, TH>(smem);
-    lk_tile<T, true, R, MODE, TH>(P.a[p], blockIdx.x - P.prefix[p], r, fp64_cond, smem, phase);
+    lk_tile<T, true, R, MODE, TH>(P.a[p], &P.m[p], blockIdx.x - P.prefix[p], r, fp64_cond, smem, phase);
 }
 
 // The window sums of five given planes, through the same passes as the iteration tile.
@@ -76,26 +77,38 @@ window_sums_kernel(const float *ch, int H, int W, int r, int tiles_x, float *out
             for (int c = 0; c < 5; ++c) out[c * N + (size_t)y * W + x] = s[c];
         }
     } else {
+        // the planes of the iteration tile: channels (0, 1) and (2, 3) as float2 pairs, 4 alone
         using F = FixedTile<R>;
-        float *P = smem;
-        for (int i = threadIdx.x; i < F::RH * F::RW; i += blockDim.x) {
-            const int ry = i / F::RW, rx = i - ry * F::RW;
-            const int y = ty0 - R + ry, x = tx0 - R + rx;
+        float2 *P01 = reinterpret_cast<float2 *>(smem);
+        float2 *P23 = P01 + F::PAIR_PLANE;
+        float *P4 = reinterpret_cast<float *>(P23 + F::PAIR_PLANE);
+        for (int i = threadIdx.x; i < F::RH * F::RWE; i += blockDim.x) {
+            const int ry = i / F::RWE, rx = i - ry * F::RWE;
+            const int y = ty0 - R + ry, x = tx0 - F::RE + rx;
             const bool in = y >= 0 && y < H && x >= 0 && x < W;
-            for (int c = 0; c < 5; ++c) P[c * F::PLANE + ry * F::RWP + rx] = in ? ch[c * N + (size_t)y * W + x] : 0.0f;
+            float c[5];
+            for (int k = 0; k < 5; ++k) c[k] = in ? ch[k * N + (size_t)y * W + x] : 0.0f;
+            P01[ry * F::RWP2 + rx] = make_float2(c[0], c[1]);
+            P23[ry * F::RWP2 + rx] = make_float2(c[2], c[3]);
+            P4[ry * F::RWP1 + rx] = c[4];
         }
         __syncthreads();
-        box_h_inplace<R>(P);
+        box_h_pairs<R, LK_TH>(P01);
+        box_h_pairs<R, LK_TH>(P23);
+        box_h_single<R, LK_TH>(P4);
+        __syncthreads();
         for (int i = threadIdx.x; i < LK_TW * (LK_TH / 4); i += blockDim.x) {
             const int tx = i % LK_TW, g = i / LK_TW;
             const int x = tx0 + tx;
             if (x >= W) continue;
-            float s[5][4];
-            box_v4<R>(P, g, tx, s);
+            float2 s01[4], s23[4];
+            float s4[4];
+            box_v_planes<R, LK_TH>(P01, P23, P4, g, tx, s01, s23, s4);
             for (int j = 0; j < 4; ++j) {
                 const int y = ty0 + 4 * g + j;
                 if (y >= H) break;
-                for (int c = 0; c < 5; ++c) out[c * N + (size_t)y * W + x] = s[c][j];
+                const float s[5] = {s01[j].x, s01[j].y, s23[j].x, s23[j].y, s4[j]};
+                for (int c = 0; c < 5; ++c) out[c * N + (size_t)y * W + x] = s[c];
             }
         }
     }
@@ -110,21 +123,24 @@ template <int R> size_t radius_smem_bytes(int r, bool stage_i2)
     return lk > pyr ? lk : pyr;
 }
 
-template <typename T, int R> static cudaError_t lk_for(const IterArgs &a, int r, float fp64_cond, cudaStream_t s)
+template <typename T, int R>
+static cudaError_t lk_for(const IterArgs &a, const StageMaps &m, int r, float fp64_cond, cudaStream_t s)
 {
-    lk_iter_kernel<T, R><<<a.tiles, LK_THREADS, sizeof(float) * lk_tile_smem_floats<R>(r, a.stage_i2 != 0), s>>>(
-        a, r, fp64_cond);
+    lk_iter_kernel<T, R><<<a.tiles, LK_THREADS,
+                           sizeof(float) * lk_tile_smem_floats<R>(r, a.stage_i2 != 0, (int)sizeof(T)), s>>>(
+        a, m, r, fp64_cond);
     return cudaGetLastError();
 }
 
-template <int R> cudaError_t lk_launch(const IterArgs &a, int elem, int r, float fp64_cond, cudaStream_t s)
+template <int R>
+cudaError_t lk_launch(const IterArgs &a, const StageMaps &m, int elem, int r, float fp64_cond, cudaStream_t s)
 {
     switch (elem) {
-    case ET_U8: return lk_for<uint8_t, R>(a, r, fp64_cond, s);
-    case ET_U16: return lk_for<uint16_t, R>(a, r, fp64_cond, s);
-    case ET_F32: return lk_for<float, R>(a, r, fp64_cond, s);
-    case ET_F16: return lk_for<__half, R>(a, r, fp64_cond, s);
-    default: return lk_for<__nv_bfloat16, R>(a, r, fp64_cond, s);
+    case ET_U8: return lk_for<uint8_t, R>(a, m, r, fp64_cond, s);
+    case ET_U16: return lk_for<uint16_t, R>(a, m, r, fp64_cond, s);
+    case ET_F32: return lk_for<float, R>(a, m, r, fp64_cond, s);
+    case ET_F16: return lk_for<__half, R>(a, m, r, fp64_cond, s);
+    default: return lk_for<__nv_bfloat16, R>(a, m, r, fp64_cond, s);
     }
 }
 
@@ -141,8 +157,9 @@ template <int R> cudaError_t ws_launch(const float *ch, int H, int W, int r, flo
 template <typename T, int R, int TH>
 static cudaError_t phase_for_th(const IterPhase &P, int r, float fp64_cond, cudaStream_t s)
 {
-    const bool stage = P.a[0].stage_i2 != 0;
-    const size_t smem = sizeof(float) * lk_tile_smem_floats<R, TH>(r, stage);
+    bool stage = false;   // shared memory for the staged window if any pair stages
+    for (int i = 0; i < P.npairs; ++i) stage = stage || P.a[i].stage_i2 != 0;
+    const size_t smem = sizeof(float) * lk_tile_smem_floats<R, TH>(r, stage, (int)sizeof(T));
     const int blocks = P.prefix[P.npairs];
     switch (P.a[0].mode) {
     case FLOW_ZERO: phase_iter_kernel<T, R, FLOW_ZERO, TH><<<blocks, LK_THREADS, smem, s>>>(P, r, fp64_cond); break;
@@ -246,6 +263,27 @@ template <int R> cudaError_t phase_i1_launch(const IterPhase &P, int elem, int r
     }
 }
 
+// The tensor maps of the staged fixed-radius tile of height TH: the estimate in boxes
+// of the tile's region (RWP2 x RH elements of 8 bytes) and I2 in boxes of the window.
+template <int R, int TH> static bool stage_maps_th(const IterArgs &a, StageMaps &m, int elem)
+{
+    using F = FixedTile<R, TH>;
+    const int S = elem_bytes(elem);
+    if (a.mode == FLOW_SAME &&
+        !encode_tile_map(&m.flow, ET_FLOW2, a.fin, a.W, a.H, (size_t)a.fin_pitch * 8, F::RWP2, F::RH))
+        return false;
+    return encode_tile_map(&m.i2, elem, a.I2, a.W, a.H, (size_t)a.pitch * S, F::win_w(S), F::WIN_H);
+}
+
+template <int R> bool radius_stage_maps(const IterArgs &a, StageMaps &m, int elem, int tile_h)
+{
+    if constexpr (R == 0) {
+        return false;
+    } else {
+        return tile_h == ALT_TH ? stage_maps_th<R, ALT_TH>(a, m, elem) : stage_maps_th<R, LK_TH>(a, m, elem);
+    }
+}
+
 template <int R> void *batch_kernel_ptr(int in_format, int storage)
 {
     if (in_format == OF_U8) {
@@ -319,7 +357,7 @@ template <int R> cudaError_t radius_configure()
     return cudaSuccess;
 }
 
-template cudaError_t lk_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
+template cudaError_t lk_launch<OF_RADIUS>(const IterArgs &, const StageMaps &, int, int, float, cudaStream_t);
 template cudaError_t ws_launch<OF_RADIUS>(const float *, int, int, int, float *, cudaStream_t);
 template cudaError_t i1h_launch<OF_RADIUS>(const HessArgs &, int, int, cudaStream_t);
 template cudaError_t phase_launch<OF_RADIUS>(const IterPhase &, int, int, float, int, cudaStream_t);
@@ -327,6 +365,7 @@ template cudaError_t phase_hess_launch<OF_RADIUS>(const HessPhase &, int, int, c
 template cudaError_t phase_i1_launch<OF_RADIUS>(const IterPhase &, int, int, float, cudaStream_t);
 template cudaError_t i1_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template void *batch_kernel_ptr<OF_RADIUS>(int, int);
+template bool radius_stage_maps<OF_RADIUS>(const IterArgs &, StageMaps &, int, int);
 template cudaError_t radius_configure<OF_RADIUS>();
 template size_t radius_smem_bytes<OF_RADIUS>(int, bool);
 

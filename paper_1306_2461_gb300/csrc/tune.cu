@@ -153,6 +153,7 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
                 for (int b : occ) {
                     if (variant && (b >= 0 || sg)) continue;   // phase launches, gathered taps only
                     if (th && b >= 0) continue;                // the persistent launch has one tile height
+                    if (sg && b >= 0) continue;                // and gathers its taps
                     Tuning t;
                     t.generic_sums = gs;
                     t.stage_i2 = sg;

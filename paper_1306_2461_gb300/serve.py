@@ -4,6 +4,7 @@ the flow computation all happen in libof.so.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import time
 
@@ -69,6 +70,11 @@ class Server:
         of._check(_lib.of_server_create(ctypes.byref(c), ctypes.byref(h)), "of_server_create")
         self._h = h
         self._buf = (Result * 1024)()
+        # Each submitted frame tensor is referenced here until its result is polled: the
+        # library copies the frame when its tick runs, so the host memory must not be
+        # freed (and handed to another tensor by torch's pinned-memory cache) before that.
+        # Results of one stream are reported in submission order.
+        self._held = collections.defaultdict(collections.deque)
 
     def open_stream(self, H, W) -> int:
         i = _i32()
@@ -89,12 +95,18 @@ class Server:
         rc = _lib.of_server_submit(self._h, sid, frame.data_ptr(), u.data_ptr() if u is not None else None,
                                    v.data_ptr() if v is not None else None, int(tag), int(arrival_ns))
         of._check(rc, "of_server_submit")
+        self._held[sid].append(frame)
 
     def poll(self, timeout_us=0) -> list[dict]:
         n = _i32()
         rc = _lib.of_server_poll(self._h, self._buf, len(self._buf), ctypes.byref(n), int(timeout_us))
         of._check(rc, "of_server_poll")
-        return [{f: getattr(self._buf[i], f) for f, _ in Result._fields_} for i in range(n.value)]
+        out = [{f: getattr(self._buf[i], f) for f, _ in Result._fields_} for i in range(n.value)]
+        for r in out:
+            held = self._held.get(r["stream"])
+            if held:
+                held.popleft()
+        return out
 
     def drain(self, timeout_ms=30000):
         of._check(_lib.of_server_drain(self._h, int(timeout_ms)), "of_server_drain")
@@ -108,6 +120,7 @@ class Server:
         if self._h is not None:
             _lib.of_server_destroy(self._h)
             self._h = None
+            self._held.clear()
 
     def __del__(self):
         try:

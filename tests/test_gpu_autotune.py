@@ -43,7 +43,7 @@ def test_every_candidate_matches_the_per_pair_path(of, oracle_mod):
     torch.cuda.synchronize()
     best, cands = of.autotune_batch(flows, I1, I2, reps=2)
     print(best, cands)
-    assert len(cands) == 29 and best["ms"] == min(c["ms"] for c in cands)
+    assert len(cands) == 26 and best["ms"] == min(c["ms"] for c in cands)
     assert sum(c["branches"] == 2 for c in cands) == 5
     sc = of.batch_size_class(flows)
     t = of.tuning_get(flows[0].plan, sc)
@@ -76,7 +76,7 @@ def test_cache_file_round_trip(of, tmp_path):
     path = str(tmp_path / "tune.json")
     ent = autotune.tune(flows, I1, I2, reps=1, path=path)
     sc = of.batch_size_class(flows)
-    assert ent["size_class"] == sc and len(ent["candidates"]) == 29
+    assert ent["size_class"] == sc and len(ent["candidates"]) == 26
     of.tuning_clear()
     assert of.tuning_get(flows[0].plan, sc) is None
     assert autotune.load(path) == 1
@@ -190,12 +190,14 @@ def test_phase_launches_in_batches_with_reuse_and_in_the_server(of):
     with serve.Server(levels=3, radius=4, iterations=3, bits=12, storage="f16", max_batch=8) as srv:
         sids = [srv.open_stream(H, W) for H, W in sizes]
         outs = {}
+        # the host frames stay referenced until the server has copied them
+        pinned = [[serve.pinned_frame(f) for f in fr] for fr in frames]
         for j in range(3):
             for k, sid in enumerate(sids):
                 u = torch.empty(sizes[k], device="cuda")
                 v = torch.empty(sizes[k], device="cuda")
                 outs[(k, j)] = (u, v)
-                srv.submit(sid, serve.pinned_frame(frames[k][j]), u, v, tag=10 * k + j)
+                srv.submit(sid, pinned[k][j], u, v, tag=10 * k + j)
         srv.drain()
         res = srv.poll(0)
         assert all(r["status"] == 0 for r in res)
