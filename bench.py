@@ -258,8 +258,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="run the batched launch with the default tuning")
     ap.add_argument("--tile-h", type=int, default=0,
                     help="with --no-autotune: the iteration tile height of the forced tuning (0: the default)")
-    ap.add_argument("--stage", type=int, default=0,
-                    help="with --no-autotune: 1 stages each tile's flow and I2 window in shared memory (TMA)")
+    ap.add_argument("--stage", type=int, default=1,
+                    help="with --no-autotune: 1 (default) stages each tile's estimate and I2 window in shared "
+                         "memory with TMA copies, 0 gathers them from global memory")
     ap.add_argument("--branches", type=int, default=0,
                     help="with --no-autotune: the default tuning in this many concurrent launch sequences")
     ap.add_argument("--i1grad", action="store_true",
@@ -314,7 +315,7 @@ def main():
     if not args.no_autotune:
         from paper_1306_2461_gb300 import autotune
         tuning = autotune.tune(flows, I1, I2, us, vs, stream=stream, reps=2, save=False)
-    elif args.branches > 1 or args.tile_h or args.stage:
+    elif args.branches > 1 or args.tile_h or not args.stage:
         of.tuning_set(flows[0].plan, of.batch_size_class(flows), branches=max(args.branches, 0),
                       tile_h=args.tile_h, stage_i2=args.stage)
 
@@ -399,7 +400,7 @@ def main():
                    "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased",
                                                                "prefetch", "tile_h", "branches")}
                               if tuning else ("default (autotuner off)"
-                                              if args.branches <= 1 and not args.tile_h and not args.stage else
+                                              if args.branches <= 1 and not args.tile_h and args.stage else
                                               f"forced (autotuner off): tile_h {args.tile_h or 'default'}, stage "
                                               f"{args.stage}, {max(args.branches, 1)} concurrent sequences")),
                    "l2": "no flush: per-step working set ~%.1f GB >> 129 MB L2" % (

@@ -60,9 +60,9 @@ typedef enum of_storage { OF_F32 = 0, OF_F16 = 1, OF_BF16 = 2 } of_storage;
 #define OF_FLAG_ZNSSD 0x4u    /* normalise both images before the pyramid (Sect. 2.4, Eq. 2): local
                                  mean and standard deviation over a radius of 5 pixels, clipped
                                  to the image; level 0 is then stored at the storage precision */
-#define OF_FLAG_STAGE_I2 0x2u /* stage each tile's I2 footprint in shared memory with bulk async
-                                 copies instead of gathering the taps from global memory (same
-                                 results; a different trade between latency and work) */
+#define OF_FLAG_GATHER 0x2u   /* gather each iteration tile's taps and estimates from global memory
+                                 instead of staging the tile's I2 window and estimate in shared
+                                 memory with TMA tensor copies (the default); same results */
 #define OF_FLAG_I1GRAD 0x8u   /* the FOLKI-lineage variant (Sect. 2.4): linearise with the gradient
                                  of the FIRST image at integer pixels (central difference, clamped)
                                  instead of the second image's gradient at the displaced position.
@@ -165,7 +165,9 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
  * locked) for the copies to be asynchronous; device buffers are caller-owned, sized
  * as in of_compute. The call is complete (fields in hus/hvs) when `stream` reaches it.
  * Errors as of_compute_batch; an error after the first chunk was queued leaves the
- * earlier chunks queued.
+ * earlier chunks queued, and `stream` waits for all of them (uploads, launches and
+ * downloads) before the call returns, so synchronising `stream` after an error makes
+ * every buffer of the call free for reuse.
  */
 int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1s, const void *const *hI2s,
                           float *const *hus, float *const *hvs, void *const *dI1s, void *const *dI2s,
@@ -176,11 +178,13 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  * batch shape has the same results to within the stated tolerances whichever tuning
  * runs it; with grouped sums (generic_sums == 0) they are the results of of_compute bit
  * for bit (with the default tile height). Without a table entry a batch runs
- * {generic_sums 0, stage_i2 0, blocks_per_sm 0, phased 1, prefetch 0, tile_h 20, branches 1}.
+ * {generic_sums 0, stage_i2 1, blocks_per_sm 0, phased 1, prefetch 0, tile_h 24, branches 1}.
  * A tuning:
  *   generic_sums   1: per-output window sums of the run-time-radius kernel;
  *                  0: grouped sums of the kernel specialised for the radius
- *   stage_i2       1: stage I2 footprints in shared memory (specialised kernel only)
+ *   stage_i2       1: stage each tile's I2 window and estimate in shared memory with TMA tensor
+ *                  copies (specialised kernel, phase launches; ignored under OF_FLAG_GATHER);
+ *                  0: gather them from global memory
  *   blocks_per_sm  resident blocks per SM of the persistent launch; 0 = as many as fit
  *   phased         1: one ordinary launch per phase (pyramid pass, iteration) over all
  *                  pairs' tiles, the pairs' arguments passed as kernel parameters, in
@@ -189,7 +193,7 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  *   prefetch       phase launches: each iteration block warms L2 with the rows the block
  *                  prefetch x (number of SMs) tiles later will read first (0: off, <= 16)
  *   tile_h         phase launches with grouped sums: height of the 64-wide iteration tile,
- *                  20 (the default; 0 means the default) or 32. Tiles other than the
+ *                  24 (the default; 0 means the default) or 32. Tiles other than the
  *                  default move each tile's reference flow, so their fields differ from
  *                  of_compute's by rounding (within the stated tolerances)
  *   branches       phase launches: the pairs split into this many groups of about equal
@@ -240,14 +244,18 @@ int of_tuning_clear(void);
  * loop (cudaMalloc/cudaFree can synchronise the device and stall the camera pipeline)
  * or a host application that owns all device memory through its own allocator.
  * The workspace of of_create lives here in one static device array of
- * OF_NOALLOC_MAX_BYTES (32 MiB: enough for one 1024 x 1024 pair at any storage),
- * reserved on every GPU where the library's code is loaded and held until exit.
+ * OF_NOALLOC_MAX_BYTES (32 MiB: enough for one 1024 x 1024 pair at any storage without
+ * OF_FLAG_I1GRAD, whose window matrices add 16 bytes per pixel), reserved on every GPU
+ * where the library's code is loaded and held until exit.
  *  p:      the plan, as for of_create; plans whose of_workspace_bytes exceed
  *          OF_NOALLOC_MAX_BYTES are rejected with OF_ENOMEM before anything is queued.
  *  I1, I2, u, v, stream: as for of_compute, except that I1 must not be NULL (there is
  *          no handle, so no previous pyramid to reuse): OF_EINVAL.
  * Nothing is allocated, on the device or by a library routine: kernels are launched
- * directly on `stream` (no graph), and the status word is cleared with a memset.
+ * directly on `stream` (no graph), and the status word is cleared with a memset. The
+ * iteration tiles always run gathered (as with OF_FLAG_GATHER, same fields as
+ * of_compute): that form has no bounded device-side wait, so no device-side error can
+ * arise that this call, having no handle to report it on, would drop.
  * The first call on a device, with that device current, looks up the array's device
  * address and sets kernel attributes; make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents: calls whose
@@ -317,7 +325,7 @@ typedef struct of_server_config {
     int32_t levels, radius, iterations; /* the method, as in of_plan, shared by all streams */
     int32_t in_format, in_bits, storage;
     float fp64_cond;
-    uint32_t flags;                     /* OF_FLAG_STAGE_I2 (OF_FLAG_NO_GRAPH is ignored) */
+    uint32_t flags;                     /* OF_FLAG_GATHER (OF_FLAG_NO_GRAPH is ignored) */
     uint64_t hbm_budget_bytes;          /* device memory all open streams may hold together */
     int32_t max_batch;                  /* pairs per tick, 1..4096 */
     int32_t max_inflight;               /* ticks queued on the device at once, 1..8 */

@@ -97,8 +97,8 @@ bool same_method(const of_plan &a, const of_plan &b)
     return a.levels == b.levels && a.radius == b.radius && a.iterations == b.iterations &&
            a.in_format == b.in_format && a.in_bits == b.in_bits && a.storage == b.storage &&
            a.fp64_cond == b.fp64_cond &&
-           (a.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD)) ==
-               (b.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD));
+           (a.flags & (OF_FLAG_GATHER | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD)) ==
+               (b.flags & (OF_FLAG_GATHER | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD));
 }
 
 // The host image of one batch: descriptors, work-list prefix sums, slots, launch shape.
@@ -245,7 +245,7 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
 {
     const int L = p0.levels;
     const bool zn = (p0.flags & OF_FLAG_ZNSSD) != 0;
-    const int32_t stage = (!t.generic_sums && ((p0.flags & OF_FLAG_STAGE_I2) || t.stage_i2)) ? 1 : 0;
+    const int32_t stage = (!t.generic_sums && !(p0.flags & OF_FLAG_GATHER) && t.stage_i2) ? 1 : 0;
     // L2 prefetch distance of the iteration launches: t.prefetch blocks per SM ahead
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -380,16 +380,35 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
     return cudaSuccess;
 }
 
-// Side streams and events of the concurrent launch sequences, per device for the life of
-// the process. Used by run_batch only, under g_mu, so one batch at a time forks on them.
+// Side streams and events of the concurrent launch sequences, per calling thread and
+// device, kept until the thread exits (work still queued on them runs to completion).
+// Batches launched directly (no graph) from different threads therefore queue their
+// extra sequences on different streams and do not wait for one another; a thread's own
+// batches share its side streams. Inside a capture the forks become graph branches.
 struct Forks {
     cudaStream_t s[3] = {};
     cudaEvent_t fork = nullptr, join[3] = {};
 };
 
+struct ThreadForks {
+    std::map<int, Forks> all;
+    ~ThreadForks()
+    {
+        for (auto &kv : all) {
+            Forks &f = kv.second;
+            if (f.fork) cudaEventDestroy(f.fork);
+            for (int b = 0; b < 3; ++b) {
+                if (f.s[b]) cudaStreamDestroy(f.s[b]);
+                if (f.join[b]) cudaEventDestroy(f.join[b]);
+            }
+        }
+    }
+};
+
 static Forks *forks_for_device()
 {
-    static std::map<int, Forks> all;
+    thread_local ThreadForks forks;
+    std::map<int, Forks> &all = forks.all;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     auto it = all.find(dev);
@@ -578,7 +597,7 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
         memcpy(k + pairs_bytes, b.prefix.data(), prefix_bytes);
         memcpy(k + pairs_bytes + prefix_bytes, &st, sizeof(st));
         const int extra[7] = {p0.radius,
-                              (int)(p0.iterations * 16 + (p0.flags & (OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD))),
+                              (int)(p0.iterations * 16 + (p0.flags & (OF_FLAG_GATHER | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD))),
                               hs[0]->device, t.generic_sums, t.stage_i2,
                               t.blocks_per_sm + 256 * t.phased + 65536 * t.prefetch + (1 << 24) * (t.tile_h != 0),
                               t.phased ? t.branches : 0};

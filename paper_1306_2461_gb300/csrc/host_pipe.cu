@@ -117,6 +117,18 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
         cudaStreamWaitEvent(pp.down, start, 0) != cudaSuccess ||
         (aux != st && cudaStreamWaitEvent(aux, start, 0) != cudaSuccess))
         return OF_ECUDA;
+    // After an error past this point, `st` is made to wait for everything already queued
+    // on the pipeline's streams before the call returns, so that a caller who synchronises
+    // `st` after the error may free or reuse the buffers of the earlier chunks.
+    auto fail = [&](int rc) {
+        for (cudaStream_t x : {pp.up, aux, pp.down}) {
+            if (x == st) continue;
+            cudaEvent_t j = pp.make();
+            if (!j || cudaEventRecord(j, x) != cudaSuccess || cudaStreamWaitEvent(st, j, 0) != cudaSuccess)
+                cudaStreamSynchronize(x);   // cannot be ordered on the device: wait here
+        }
+        return rc;
+    };
     const size_t in_elem = hs[0]->plan.in_format == OF_U8 ? 1 : 2;
     std::vector<const void *> d1(per);
     for (int c = 0; c < nch; ++c) {
@@ -125,27 +137,27 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
             const size_t px = (size_t)hs[i]->plan.H * hs[i]->plan.W;
             if ((hI1s[i] && cudaMemcpyAsync(dI1s[i], hI1s[i], px * in_elem, cudaMemcpyHostToDevice, pp.up) != cudaSuccess) ||
                 cudaMemcpyAsync(dI2s[i], hI2s[i], px * in_elem, cudaMemcpyHostToDevice, pp.up) != cudaSuccess)
-                return OF_ECUDA;
+                return fail(OF_ECUDA);
             d1[i - off] = hI1s[i] ? dI1s[i] : nullptr;
         }
         cudaStream_t cs = (c & 1) ? aux : st;
         cudaEvent_t in = pp.make(), done = pp.make();
         if (!in || !done || cudaEventRecord(in, pp.up) != cudaSuccess || cudaStreamWaitEvent(cs, in, 0) != cudaSuccess)
-            return OF_ECUDA;
+            return fail(OF_ECUDA);
         const Tuning t = tuning_for(hs[0]->plan, batch_size_class(cnt, hs + off));
         const int rc = run_batch(cnt, hs + off, d1.data(), dI2s + off, dus + off, dvs + off, cs, t);
-        if (rc != OF_OK) return rc;
+        if (rc != OF_OK) return fail(rc);
         if (cudaEventRecord(done, cs) != cudaSuccess || cudaStreamWaitEvent(pp.down, done, 0) != cudaSuccess)
-            return OF_ECUDA;
+            return fail(OF_ECUDA);
         for (int i = off; i < off + cnt; ++i) {
             const size_t bytes = (size_t)hs[i]->plan.H * hs[i]->plan.W * sizeof(float);
             if (cudaMemcpyAsync(hus[i], dus[i], bytes, cudaMemcpyDeviceToHost, pp.down) != cudaSuccess ||
                 cudaMemcpyAsync(hvs[i], dvs[i], bytes, cudaMemcpyDeviceToHost, pp.down) != cudaSuccess)
-                return OF_ECUDA;
+                return fail(OF_ECUDA);
         }
     }
     cudaEvent_t end = pp.make();
     if (!end || cudaEventRecord(end, pp.down) != cudaSuccess || cudaStreamWaitEvent(st, end, 0) != cudaSuccess)
-        return OF_ECUDA;
+        return fail(OF_ECUDA);
     return OF_OK;
 }

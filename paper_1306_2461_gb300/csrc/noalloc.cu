@@ -12,6 +12,11 @@
 // every GPU on which the library's code is loaded, held until the process exits. All
 // calls share it and it keeps whatever the last call left there; every call fully
 // rewrites the pyramids and flow buffers it reads, and clears the status word.
+//
+// The iteration tiles run in their gathered form (OF_FLAG_GATHER): the staged form waits,
+// with a time limit, for its TMA copies and reports a wait that ran out through the
+// handle's status word, which a caller without a handle could not read. The gathered
+// kernels wait for nothing and give the same fields.
 #include <string.h>
 
 #include <mutex>
@@ -64,6 +69,7 @@ extern "C" int of_compute_noalloc(const of_plan *p, const void *I1, const void *
     // of_create lays out its own workspace.
     of_ctx h;
     h.plan = *p;
+    h.plan.flags |= OF_FLAG_GATHER;   // no device-side waits, so nothing to report
     h.lay = lay;
     cudaGetDevice(&h.device);
     of::assign_workspace(&h, ws);

@@ -215,7 +215,7 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
             const int th = i1grad ? I1_TH : LK_TH;   // the variant's kernels have their own tile height
             a.tiles = a.tiles_x * ((a.H + th - 1) / th);
             a.status = h->status;
-            a.stage_i2 = (p.flags & OF_FLAG_STAGE_I2) && !i1grad ? 1 : 0;
+            a.stage_i2 = !(p.flags & OF_FLAG_GATHER) && !i1grad ? 1 : 0;
             StageMaps maps;
             memset(&maps, 0, sizeof(maps));
             if (a.stage_i2) fill_stage_maps(a, maps, level_elem(p, l), p.radius, LK_TH);   // else gathered
@@ -271,7 +271,7 @@ int of_plan_validate(const of_plan *p)
     }
     if (p->storage != OF_F32 && p->storage != OF_F16 && p->storage != OF_BF16) return OF_EINVAL;
     if (!(p->fp64_cond >= 0.0f) || isinf(p->fp64_cond)) return OF_EINVAL;
-    if (p->flags & ~(OF_FLAG_NO_GRAPH | OF_FLAG_STAGE_I2 | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD)) return OF_EINVAL;
+    if (p->flags & ~(OF_FLAG_NO_GRAPH | OF_FLAG_GATHER | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD)) return OF_EINVAL;
     return OF_OK;
 }
 

@@ -73,7 +73,7 @@ cudaError_t dev_malloc(void **p, size_t bytes);
 // How one persistent batched launch is run (the autotuner's choice; see tune.cu).
 struct Tuning {
     int generic_sums = 0;    // 1: the run-time-radius kernel (per-output sums); 0: grouped fixed-radius sums
-    int stage_i2 = 0;        // 1: stage I2 footprints in shared memory (fixed-radius kernel only)
+    int stage_i2 = 1;        // 1: stage I2 windows and estimates in shared memory (fixed-radius kernel only)
     int blocks_per_sm = 0;   // resident blocks per SM of the persistent launch; 0 = as many as fit
     int phased = 1;          // 1: one ordinary launch per phase; 0: the persistent launch with grid barriers
     int prefetch = 0;        // phase launches: warm L2 for the tile this many blocks per SM ahead (0: off)

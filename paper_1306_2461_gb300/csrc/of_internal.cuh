@@ -147,11 +147,12 @@ static_assert(sizeof(IterPhase) <= 32000 && sizeof(PyrPhase) <= 32000, "kernel p
 
 // Tile shapes.
 constexpr int LK_TW = 64;    // iteration output tile width
-// Iteration output tile: 64 x 20 (measured at the 1024^2, r = 4 batch: 64 x 32 at 3
-// blocks per SM 7.3k fields/s, 64 x 28 and 64 x 24 at 4 blocks 8.1k, 64 x 20 at 5 blocks
-// 8.3k, 64 x 16 at 6 blocks 8.1k). The height can be set at build time (a multiple of 4).
+// Iteration output tile: 64 x 24 at 4 blocks of 256 threads per SM (measured at the 1024^2,
+// r = 4 batch with staging: 64 x 24 at 4 blocks 6.66 ms per step, 64 x 32 at 3 blocks 6.87,
+// 64 x 20 at 4 blocks 7.11; with 512-thread blocks at 2 per SM 64 x 56 6.75, 64 x 48
+// 6.87). The height can be set at build time (a multiple of 4).
 #ifndef OF_LK_TH
-#define OF_LK_TH 20
+#define OF_LK_TH 24
 #endif
 constexpr int LK_TH = OF_LK_TH;
 static_assert(LK_TH % 4 == 0, "the vertical box pass takes 4 rows at a time");

@@ -540,6 +540,9 @@ template <int R, int TH = LK_TH> struct FixedTile {
         TH == LK_TH ? (R <= 6 ? OF_LK_MIN_BLOCKS : 2) : (SMEM_FIT < 1 ? 1 : (SMEM_FIT > 5 ? 5 : SMEM_FIT));
 };
 
+#ifndef OF_PREFETCH_I1
+#define OF_PREFETCH_I1 0   // staged tile: warm L2 with the region's I1 rows while its boxes land
+#endif
 constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's staging copies
 
 // o[j] = sum_{k=0}^{2R} v[j+k], j = 0..3, from v[0 .. 2R+3].
@@ -948,6 +951,12 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
             if (SAME) tma_load_2d(P01, &maps->flow, tx0 - F::RE, ty0 - R, bar);
             tma_load_2d(win, &maps->i2, wx0, wy0, bar);
         }
+#if OF_PREFETCH_I1
+        // while the boxes land: warm L2 with the region's rows of I1 (read by stage 1)
+        if (threadIdx.x >= 32 && threadIdx.x < 32 + F::RH)
+            prefetch_row(a.I1, a.pitch, S, a.H, a.W, ty0 - R, ty0 - R + F::RH, tx0 - F::RE, tx0 - F::RE + F::RWE,
+                         threadIdx.x - 32);
+#endif
         bool done = mbar_wait_bounded(bar, phase, STAGE_TIMEOUT_NS);
         if (__syncthreads_or(!done)) {
             // give the copies in flight a further bounded wait before the block leaves

@@ -19,7 +19,7 @@ OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_EDEVICE, OF_ETIMEOUT, OF_ESTATE, OF_EB
 OF_U8, OF_U16 = 0, 1
 OF_F32, OF_F16, OF_BF16 = 0, 1, 2
 OF_FLAG_NO_GRAPH = 0x1
-OF_FLAG_STAGE_I2 = 0x2
+OF_FLAG_GATHER = 0x2
 OF_FLAG_ZNSSD = 0x4
 OF_FLAG_I1GRAD = 0x8
 STORAGE = {"f32": OF_F32, "f16": OF_F16, "bf16": OF_BF16}
@@ -318,7 +318,7 @@ def tuning_get(method: Plan, size_class: int) -> dict | None:
     return t.as_dict()
 
 
-def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=0, blocks_per_sm=0, phased=1, prefetch=0,
+def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=1, blocks_per_sm=0, phased=1, prefetch=0,
                tile_h=0, branches=0):
     """of_tuning_set; the defaults are the library's tuning without a table entry."""
     t = Tuning(int(generic_sums), int(stage_i2), int(blocks_per_sm), int(phased), int(prefetch), int(tile_h),

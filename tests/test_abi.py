@@ -108,7 +108,7 @@ def test_tuning_table_host_calls(of):
     with pytest.raises(of.OfError):
         of.tuning_set(m, 20, blocks_per_sm=2, phased=1)                   # occupancy is a persistent-launch knob
     with pytest.raises(of.OfError):
-        of.tuning_set(m, 20, tile_h=24)                                   # tile heights 20 and 32 only
+        of.tuning_set(m, 20, tile_h=20)                                   # tile heights 24 and 32 only
     with pytest.raises(of.OfError):
         of.tuning_set(m, 20, tile_h=32, phased=0)                         # the persistent launch has one
     with pytest.raises(of.OfError):
@@ -127,6 +127,6 @@ def test_tuning_table_host_calls(of):
     of.tuning_set(m, 20)
     assert of.tuning_get(v, 20)["branches"] == 2
     t = of.tuning_get(m, 20)
-    assert (t["phased"], t["prefetch"], t["tile_h"], t["branches"]) == (1, 0, 20, 1)
+    assert (t["phased"], t["prefetch"], t["tile_h"], t["branches"]) == (1, 0, 24, 1)
     of.tuning_clear()
     assert of.tuning_get(m, 20) is None

@@ -93,7 +93,7 @@ def test_mixed_size_batch_64_pairs(of, oracle_mod):
 def test_batch_staged_i2_equals_single(of):
     import torch
     pairs = synth.make_batch(5, seed=9, sizes=((160, 256), (256, 256), (96, 320)))
-    flows = [of.Flow(of.Plan.make(*p.shape, 3, 4, 4, bits=8, storage="f16", flags=of.OF_FLAG_STAGE_I2))
+    flows = [of.Flow(of.Plan.make(*p.shape, 3, 4, 4, bits=8, storage="f16", flags=of.OF_FLAG_GATHER))
              for p in pairs]
     I1 = [to_dev(p.I1) for p in pairs]
     I2 = [to_dev(p.I2) for p in pairs]

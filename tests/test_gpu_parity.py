@@ -209,7 +209,7 @@ def test_staged_i2_equals_gathered(of, storage, r):
     import torch
     p = synth.make_c2(320, 448, seed=4)
     res = []
-    for flags in (0, of.OF_FLAG_STAGE_I2):
+    for flags in (0, of.OF_FLAG_GATHER):
         plan = of.Plan.make(320, 448, 3, r, 3, bits=12, storage=storage, flags=flags)
         with of.Flow(plan) as f:
             u, v = f.compute(to_dev(p.I1), to_dev(p.I2))
@@ -297,14 +297,14 @@ def test_staged_window_with_large_displacements(of, storage, H, W, d):
     I2 = np.rint(I2).astype(np.uint16)
     for r in (2, 4, 10):
         g = gpu_flow((I1, I2), 1, r, 6, storage, bits=12)
-        s = gpu_flow((I1, I2), 1, r, 6, storage, bits=12, flags=of.OF_FLAG_STAGE_I2)
+        s = gpu_flow((I1, I2), 1, r, 6, storage, bits=12, flags=of.OF_FLAG_GATHER)
         assert np.array_equal(g[0], s[0]) and np.array_equal(g[1], s[1]), r
     # and the staged path through the batched phase launches (tuning forced to staging)
     plan = of.Plan.make(H, W, 2, 4, 4, bits=12, storage=storage)
     sc = None
     with of.Flow(plan) as f:
         sc = of.batch_size_class([f])
-        of.tuning_set(plan, sc, stage_i2=1)
+        of.tuning_set(plan, sc, stage_i2=0)
         ub, vb = of.compute_batch([f], [to_dev(I1)], [to_dev(I2)])
         torch.cuda.synchronize()
     of.tuning_clear()
