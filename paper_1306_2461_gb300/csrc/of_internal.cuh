@@ -173,7 +173,7 @@ static_assert(I1_TH % 4 == 0, "the vertical box pass takes 4 rows at a time");
 #define OF_LK_THREADS 256
 #endif
 constexpr int LK_THREADS = OF_LK_THREADS;   // threads per iteration / batch block
-constexpr int PYR_TW = 32;   // pyramid output tile
+constexpr int PYR_TW = 64;   // pyramid output tile
 constexpr int PYR_TH = 16;
 constexpr int PYR_THREADS = 256;
 #ifndef OF_MAX_RADIUS

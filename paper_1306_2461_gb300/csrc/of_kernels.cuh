@@ -36,10 +36,14 @@ template <bool NC> __device__ __forceinline__ float ldf(const __nv_bfloat16 *p)
 __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
 
 // ------------------------------------------------------------------ pyramid tile
-// Shared memory: PYR_SMEM_FLOATS floats.
+// An output tile of PYR_TW x PYR_TH at level l+1 reads rows 2 ty0 - 2 .. 2 ty0 + 2 PYR_TH
+// (PYR_RH rows) of level l and, per row, PYR_RWS(T) columns starting one 16-byte chunk
+// left of 2 tx0 (the 5-tap window needs 2 tx0 - 2 .. 2 tx0 + 2 PYR_TW).
 constexpr int PYR_RH = 2 * PYR_TH + 3;
-constexpr int PYR_RW = 2 * PYR_TW + 3;
-constexpr int PYR_SMEM_FLOATS = PYR_RH * PYR_RW + PYR_RH * PYR_TW;
+template <typename T> constexpr int pyr_chunk() { return 16 / (int)sizeof(T); }   // elements per 16 bytes
+template <typename T> constexpr int pyr_rws() { return 2 * PYR_TW + 2 * pyr_chunk<T>(); }
+template <typename T> constexpr int pyr_smem_floats() { return PYR_RH * pyr_rws<T>() + PYR_RH * PYR_TW; }
+constexpr int PYR_SMEM_FLOATS = PYR_RH * (2 * PYR_TW + 32) + PYR_RH * PYR_TW;   // the largest (8-bit input)
 
 // The pair of block b in a phase launch: the largest p with prefix[p] <= b.
 __device__ __forceinline__ int phase_pair(const int32_t *prefix, int n, int b)
@@ -106,67 +110,106 @@ __device__ __forceinline__ float binom5(float a, float b, float c, float d, floa
     return fmaf(6.0f, c, fmaf(4.0f, __fadd_rn(b, d), __fadd_rn(a, e)));
 }
 
-// One output tile (PYR_TH x PYR_TW at level l+1) of image `img` (0/1) of a pair.
+// The elements of one 16-byte chunk as floats.
+template <typename T> __device__ __forceinline__ void chunk_to_f(const uint4 &w, float *o)
+{
+    const T *e = reinterpret_cast<const T *>(&w);
+#pragma unroll
+    for (int k = 0; k < pyr_chunk<T>(); ++k) o[k] = ldf<false>(e + k);
+}
+
+// One output tile (PYR_TW x PYR_TH at level l+1) of image `img` (0/1) of a pair.
 // FIRST: the source is the raw camera image; level 0 is stored as well, unchanged in
-// the camera's integer format.
+// the camera's integer format. Rows are read in 16-byte chunks (each thread one chunk at a
+// time, converted to FP32 in shared memory once); the chunks of FIRST's level-0 copy are
+// stored from the same registers. Chunks that cross the image border, or all of them when
+// a row is not 16-byte aligned, are read element by element with clamped coordinates.
+// Then the horizontal and the vertical binomial, 4 outputs per thread with 16-byte
+// shared-memory accesses.
 template <typename Tin, typename Tout, bool FIRST, bool NC>
 __device__ __forceinline__ void pyr_tile_smem(const PyrArgs &a, int tile, int img, float *smem)
 {
-    float *s_in = smem;                      // PYR_RH x PYR_RW
-    float *s_h = smem + PYR_RH * PYR_RW;     // PYR_RH x PYR_TW
+    constexpr int CH = pyr_chunk<Tin>();
+    constexpr int RWS = pyr_rws<Tin>();
+    constexpr int NCH = RWS / CH;   // chunks per row
+    float *s_in = smem;                          // PYR_RH x RWS
+    float *s_h = smem + PYR_RH * RWS;           // PYR_RH x PYR_TW
     const int ty0 = (tile / a.tiles_x) * PYR_TH;
     const int tx0 = (tile - (tile / a.tiles_x) * a.tiles_x) * PYR_TW;
-    const int ys = 2 * ty0 - 2, xs = 2 * tx0 - 2;
+    const int ys = 2 * ty0 - 2, cs = 2 * tx0 - CH;
     const Tin *src = static_cast<const Tin *>(img ? a.src[1] : a.src[0]);
+    Tin *d0 = FIRST ? static_cast<Tin *>(img ? a.dst0[1] : a.dst0[0]) : nullptr;
+    const bool vsrc = (a.src_pitch * (int)sizeof(Tin)) % 16 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    const bool vdst = FIRST && (a.dst0_pitch * (int)sizeof(Tin)) % 16 == 0 && (reinterpret_cast<uintptr_t>(d0) & 15) == 0;
     __syncthreads();   // the previous tile's readers of smem are done
-    for (int i = threadIdx.x; i < PYR_RH * PYR_RW; i += blockDim.x) {
-        const int r = i / PYR_RW, c = i - r * PYR_RW;
-        const int y = clampi(ys + r, 0, a.H - 1), x = clampi(xs + c, 0, a.W - 1);
-        s_in[i] = ldf<NC>(src + (size_t)y * a.src_pitch + x);
+    for (int i = threadIdx.x; i < PYR_RH * NCH; i += blockDim.x) {
+        const int r = i / NCH, k = i - r * NCH;
+        const int y = ys + r, c0 = cs + k * CH;
+        float v[CH];
+        const bool inside = vsrc && (unsigned)y < (unsigned)a.H && c0 >= 0 && c0 + CH <= a.W;
+        if (inside) {
+            const uint4 w = ld<NC>(reinterpret_cast<const uint4 *>(src + ((size_t)y * a.src_pitch + c0)));
+            chunk_to_f<Tin>(w, v);
+            // level 0 as it is: the tile's rows 2 ty0 .. 2 ty0 + 2 PYR_TH - 1, columns 2 tx0 ..
+            if (FIRST && vdst && r >= 2 && r < 2 + 2 * PYR_TH && k >= 1 && k <= 2 * PYR_TW / CH)
+                *reinterpret_cast<uint4 *>(d0 + ((size_t)y * a.dst0_pitch + c0)) = w;
+        } else {
+            const int yc = clampi(y, 0, a.H - 1);
+#pragma unroll
+            for (int e = 0; e < CH; ++e)
+                v[e] = ldf<NC>(src + ((size_t)yc * a.src_pitch + clampi(c0 + e, 0, a.W - 1)));
+        }
+        if (FIRST && !(inside && vdst) && r >= 2 && r < 2 + 2 * PYR_TH && k >= 1 && k <= 2 * PYR_TW / CH &&
+            (unsigned)y < (unsigned)a.H) {
+#pragma unroll
+            for (int e = 0; e < CH; ++e)
+                if ((unsigned)(c0 + e) < (unsigned)a.W) d0[(size_t)y * a.dst0_pitch + c0 + e] = to_elem<Tin>(v[e]);
+        }
+        float4 *q = reinterpret_cast<float4 *>(s_in + r * RWS + k * CH);
+#pragma unroll
+        for (int e = 0; e < CH / 4; ++e) q[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
     }
     __syncthreads();
-    if (FIRST) {
-        Tin *d0 = static_cast<Tin *>(img ? a.dst0[1] : a.dst0[0]);
-        // the tile's level-0 pixels, as they are: 16-byte chunks straight from the camera
-        // image when its rows allow it and the tile lies inside the image, else element
-        // by element from shared memory (the same values either way)
-        constexpr int E = 16 / (int)sizeof(Tin);
-        constexpr int CPR = 2 * PYR_TW / E;   // chunks per tile row
-        const bool chunks = 2 * tx0 + 2 * PYR_TW <= a.W && 2 * ty0 + 2 * PYR_TH <= a.H &&
-                            (a.src_pitch * (int)sizeof(Tin)) % 16 == 0 && (a.dst0_pitch * (int)sizeof(Tin)) % 16 == 0 &&
-                            (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(d0) & 15) == 0;
-        if (chunks) {
-            for (int i = threadIdx.x; i < 2 * PYR_TH * CPR; i += blockDim.x) {
-                const int r = i / CPR, c = i - r * CPR;
-                const int y = 2 * ty0 + r, x = 2 * tx0 + c * E;
-                *reinterpret_cast<uint4 *>(d0 + (size_t)y * a.dst0_pitch + x) =
-                    ld<NC>(reinterpret_cast<const uint4 *>(src + (size_t)y * a.src_pitch + x));
-            }
-        } else {
-            for (int i = threadIdx.x; i < 4 * PYR_TH * PYR_TW; i += blockDim.x) {
-                const int r = i / (2 * PYR_TW), c = i - r * (2 * PYR_TW);
-                const int y = 2 * ty0 + r, x = 2 * tx0 + c;
-                if (y < a.H && x < a.W)
-                    d0[(size_t)y * a.dst0_pitch + x] = to_elem<Tin>(s_in[(r + 2) * PYR_RW + c + 2]);
-            }
-        }
-    }
     Tout *d = static_cast<Tout *>(img ? a.dst[1] : a.dst[0]);
     if (d == nullptr) return;   // one-level plan: level 0 only (uniform per block)
-    for (int i = threadIdx.x; i < PYR_RH * PYR_TW; i += blockDim.x) {
-        const int r = i / PYR_TW, j = i - r * PYR_TW;
-        const float *q = s_in + r * PYR_RW + 2 * j;
-        s_h[i] = binom5(q[0], q[1], q[2], q[3], q[4]);
+    // horizontal: outputs 4g .. 4g + 3 of a row read columns 8g - 2 + CH .. 8g + 8 + CH
+    // (image 2 (tx0 + 4g) - 2 ..), from the 16 floats starting at column 8g + CH - 4
+    constexpr int NG = PYR_TW / 4;
+    for (int i = threadIdx.x; i < PYR_RH * NG; i += blockDim.x) {
+        const int r = i / NG, g = i - r * NG;
+        const float4 *q = reinterpret_cast<const float4 *>(s_in + r * RWS + 8 * g + CH - 4);
+        float v[16];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float4 t = q[e];
+            v[4 * e] = t.x;
+            v[4 * e + 1] = t.y;
+            v[4 * e + 2] = t.z;
+            v[4 * e + 3] = t.w;
+        }
+        float o[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) o[jj] = binom5(v[2 + 2 * jj], v[3 + 2 * jj], v[4 + 2 * jj], v[5 + 2 * jj], v[6 + 2 * jj]);
+        *reinterpret_cast<float4 *>(s_h + r * PYR_TW + 4 * g) = make_float4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < PYR_TH * PYR_TW; i += blockDim.x) {
-        const int r = i / PYR_TW, j = i - r * PYR_TW;
-        const int y = ty0 + r, x = tx0 + j;
-        if (y < a.Ho && x < a.Wo) {
-            const float *q = s_h + 2 * r * PYR_TW + j;
-            const float s = binom5(q[0], q[PYR_TW], q[2 * PYR_TW], q[3 * PYR_TW], q[4 * PYR_TW]);
-            d[(size_t)y * a.dst_pitch + x] = to_elem<Tout>(s * (1.0f / 256.0f));
-        }
+    // vertical: output row i reads rows 2i .. 2i + 4 of s_h
+    for (int i = threadIdx.x; i < PYR_TH * NG; i += blockDim.x) {
+        const int r = i / NG, g = i - r * NG;
+        const int y = ty0 + r, x = tx0 + 4 * g;
+        if (y >= a.Ho || x >= a.Wo) continue;
+        float4 c[5];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) c[e] = *reinterpret_cast<const float4 *>(s_h + (2 * r + e) * PYR_TW + 4 * g);
+        const float o0 = binom5(c[0].x, c[1].x, c[2].x, c[3].x, c[4].x) * (1.0f / 256.0f);
+        const float o1 = binom5(c[0].y, c[1].y, c[2].y, c[3].y, c[4].y) * (1.0f / 256.0f);
+        const float o2 = binom5(c[0].z, c[1].z, c[2].z, c[3].z, c[4].z) * (1.0f / 256.0f);
+        const float o3 = binom5(c[0].w, c[1].w, c[2].w, c[3].w, c[4].w) * (1.0f / 256.0f);
+        Tout *row = d + (size_t)y * a.dst_pitch + x;
+        row[0] = to_elem<Tout>(o0);
+        if (x + 1 < a.Wo) row[1] = to_elem<Tout>(o1);
+        if (x + 2 < a.Wo) row[2] = to_elem<Tout>(o2);
+        if (x + 3 < a.Wo) row[3] = to_elem<Tout>(o3);
     }
 }
 
@@ -668,6 +711,25 @@ __device__ __forceinline__ void flow_pair(const IterArgs &a, int x, int y, bool 
             return;
         }
     }
+    if (MODE == FLOW_UPSAMPLE || (MODE < 0 && a.mode == FLOW_UPSAMPLE)) {
+        // flow_at_m's upsampling for x (weight 0) and x + 1 (weight 1/2), which share
+        // their four coarse samples (x even), computed on both at once
+        const int x0 = x >> 1, y0 = y >> 1;
+        const int x1 = min(x0 + 1, a.Wc - 1), y1 = min(y0 + 1, a.Hc - 1);
+        const float ay = (y & 1) ? 0.5f : 0.0f;
+        const float2 *r0 = a.fin + y0 * a.fin_pitch, *r1 = a.fin + y1 * a.fin_pitch;
+        const float2 f00 = ld<NC>(r0 + x0), f01 = ld<NC>(r0 + x1);
+        const float2 f10 = ld<NC>(r1 + x0), f11 = ld<NC>(r1 + x1);
+        const float2 T = f2(0.0f, 0.5f), OT = f2(1.0f, 0.5f), AY = f2(ay, ay), OY = f2(1.0f - ay, 1.0f - ay);
+        const float2 two = f2(2.0f, 2.0f);
+        const float2 ux = mul2(two, lerp2(lerp2(f2(f00.x, f00.x), f2(f01.x, f01.x), T, OT),
+                                          lerp2(f2(f10.x, f10.x), f2(f11.x, f11.x), T, OT), AY, OY));
+        const float2 uy = mul2(two, lerp2(lerp2(f2(f00.y, f00.y), f2(f01.y, f01.y), T, OT),
+                                          lerp2(f2(f10.y, f10.y), f2(f11.y, f11.y), T, OT), AY, OY));
+        fp = f2(ux.x, uy.x);
+        fq = q ? f2(ux.y, uy.y) : f2(0.0f, 0.0f);
+        return;
+    }
     fp = flow_mode<NC, MODE>(a, x, y);
     fq = q ? flow_mode<NC, MODE>(a, x + 1, y) : f2(0.0f, 0.0f);
 }
@@ -680,21 +742,20 @@ __device__ __forceinline__ bool interior(float px, float py, int H, int W)
 // The interior branch of sample_grad for two sample positions at once (X, Y: their
 // coordinates), with every operation of the scalar form on both components. The 12 taps
 // of each come from the staged window (win: WW x WH elements, first element at image
-// (wx0, wy0)) when both 4x4 footprints lie inside it, else from global memory.
+// (wx0, wy0)) when `inwin`, else from global memory. FX, FY: floor(X), floor(Y).
 template <bool NC, int WW, typename T>
-__device__ __forceinline__ void sample_grad2(const T *I, int pitch, const T *win, int wx0, int wy0, int WH, float2 X,
-                                             float2 Y, float2 &IW, float2 &GX, float2 &GY)
+__device__ __forceinline__ void sample_grad2(const T *I, int pitch, const T *win, bool inwin, int cpx, int cpy,
+                                             int cqx, int cqy, float2 X, float2 Y, float2 FX, float2 FY, float2 &IW,
+                                             float2 &GX, float2 &GY)
 {
-    const float2 FX = f2(floorf(X.x), floorf(X.y)), FY = f2(floorf(Y.x), floorf(Y.y));
     const float2 AX = sub2(X, FX), AY = sub2(Y, FY);
     const float2 one = f2(1.0f, 1.0f);
     const float2 OX = sub2(one, AX), OY = sub2(one, AY);
-    const int xp = (int)FX.x, yp = (int)FY.x, xq = (int)FX.y, yq = (int)FY.y;
     float2 A0, A1, BM, B0, B1, B2, CM, C0, C1, C2, D0, D1;
-    if (win && xp - 1 >= wx0 && xq - 1 >= wx0 && xp + 2 < wx0 + WW && xq + 2 < wx0 + WW && yp - 1 >= wy0 &&
-        yq - 1 >= wy0 && yp + 2 < wy0 + WH && yq + 2 < wy0 + WH) {
-        // rows WW elements apart: every tap at a constant offset from the pixel's corner
-        const T *p = win + ((yp - 1 - wy0) * WW + (xp - wx0)), *q = win + ((yq - 1 - wy0) * WW + (xq - wx0));
+    if (inwin) {
+        // (cpx, cpy), (cqx, cqy): the taps' top-left corner (x0 - 1, y0 - 1) in the window;
+        // rows WW elements apart: every tap at a constant offset from it
+        const T *p = win + (cpy * WW + cpx + 1), *q = win + (cqy * WW + cqx + 1);
         A0 = f2(ldf<false>(p), ldf<false>(q));
         A1 = f2(ldf<false>(p + 1), ldf<false>(q + 1));
         BM = f2(ldf<false>(p + WW - 1), ldf<false>(q + WW - 1));
@@ -708,6 +769,7 @@ __device__ __forceinline__ void sample_grad2(const T *I, int pitch, const T *win
         D0 = f2(ldf<false>(p + 3 * WW), ldf<false>(q + 3 * WW));
         D1 = f2(ldf<false>(p + 3 * WW + 1), ldf<false>(q + 3 * WW + 1));
     } else {
+        const int xp = (int)FX.x, yp = (int)FY.x, xq = (int)FX.y, yq = (int)FY.y;
         const int op = (yp - 1) * pitch + xp, oq = (yq - 1) * pitch + xq;
         const T *mp = I + op, *mq = I + oq;
         const T *p0 = I + (op + pitch), *q0 = I + (oq + pitch);
@@ -855,8 +917,8 @@ __device__ __forceinline__ void box_v_planes(const float2 *P01, const float2 *P2
 // products in the planes' layout.
 template <typename T, bool NC, int MODE, int WW>
 __device__ __forceinline__ void stage1_pair(const IterArgs &a, int x, int y, float2 ref, const float4 *sflow,
-                                            const T *win, int wx0, int wy0, int WH, float4 &s01, float4 &s23,
-                                            float2 &s4)
+                                            const T *win, bool win_in_image, int wx0, int wy0, int WH, float4 &s01,
+                                            float4 &s23, float2 &s4)
 {
     s01 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     s23 = s01;
@@ -879,8 +941,18 @@ __device__ __forceinline__ void stage1_pair(const IterArgs &a, int x, int y, flo
     const float2 X = add2(f2((float)x, (float)(x + 1)), f2(fp.x, fq.x));
     const float2 Y = add2(f2((float)y, (float)y), f2(fp.y, fq.y));
     float2 IW, GX, GY;
-    if (inq && interior(X.x, Y.x, a.H, a.W) && interior(X.y, Y.y, a.H, a.W)) {
-        sample_grad2<NC, WW>(I2, a.pitch, win, wx0, wy0, WH, X, Y, IW, GX, GY);
+    // Both pixels sample the interior (their 4x4 footprints inside the image) and, with a
+    // staged window, the footprints' corners (x0 - 1, y0 - 1) inside it. When the whole
+    // window lies inside the image, a footprint inside the window is inside the image,
+    // which is the interior condition, so only the window is tested.
+    const float2 FX = f2(floorf(X.x), floorf(X.y)), FY = f2(floorf(Y.x), floorf(Y.y));
+    const int cpx = (int)FX.x - 1 - wx0, cpy = (int)FY.x - 1 - wy0;
+    const int cqx = (int)FX.y - 1 - wx0, cqy = (int)FY.y - 1 - wy0;
+    const bool inwin = win && (unsigned)cpx < (unsigned)(WW - 3) && (unsigned)cqx < (unsigned)(WW - 3) &&
+                       (unsigned)cpy < (unsigned)(WH - 3) && (unsigned)cqy < (unsigned)(WH - 3);
+    if (inq && (win_in_image ? inwin
+                             : (interior(X.x, Y.x, a.H, a.W) && interior(X.y, Y.y, a.H, a.W)))) {
+        sample_grad2<NC, WW>(I2, a.pitch, win, inwin, cpx, cpy, cqx, cqy, X, Y, FX, FY, IW, GX, GY);
     } else {
         float iw0, gx0, gy0, iw1 = 0.0f, gx1 = 0.0f, gy1 = 0.0f;
         sample_grad<NC>(I2, a.pitch, a.H, a.W, X.x, Y.x, iw0, gx0, gy0);
@@ -970,18 +1042,28 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
     constexpr int NPR = F::RWE / 2;   // pairs per region row
     constexpr int NPAIR = F::RH * NPR;
     const T *wt = staged ? reinterpret_cast<const T *>(win) : nullptr;
+    const bool win_in_image = staged && wx0 >= 0 && wy0 >= 0 && wx0 + WW <= a.W && wy0 + F::WIN_H <= a.H;
+    // pair j = threadIdx.x + k LK_THREADS is (row ry, pair cx) of the region: stepped
+    // without a division (LK_THREADS = DY rows + DX pairs)
+    constexpr int DY = LK_THREADS / NPR, DX = LK_THREADS % NPR;
+    int ry = threadIdx.x / NPR, cx = threadIdx.x % NPR;
 #pragma unroll 1
     for (int j = threadIdx.x; j < NPAIR; j += LK_THREADS) {
-        const int ry = j / NPR, cx = j - ry * NPR;
         const int k2 = ry * (F::RWP2 / 2) + cx;   // float4 slot of the pair in the pair planes
         float4 s01, s23;
         float2 s4;
         stage1_pair<T, NC, MODE, WW>(a, tx0 - F::RE + 2 * cx, ty0 - R + ry, ref,
-                                     (SAME && staged) ? reinterpret_cast<const float4 *>(P01) + k2 : nullptr, wt, wx0,
-                                     wy0, F::WIN_H, s01, s23, s4);
+                                     (SAME && staged) ? reinterpret_cast<const float4 *>(P01) + k2 : nullptr, wt,
+                                     win_in_image, wx0, wy0, F::WIN_H, s01, s23, s4);
         reinterpret_cast<float4 *>(P01)[k2] = s01;
         reinterpret_cast<float4 *>(P23)[k2] = s23;
         reinterpret_cast<float2 *>(P4)[ry * (F::RWP1 / 2) + cx] = s4;
+        ry += DY;
+        cx += DX;
+        if (cx >= NPR) {
+            cx -= NPR;
+            ++ry;
+        }
     }
     __syncthreads();
     box_h_pairs<R, TH>(P01);
