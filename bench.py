@@ -110,6 +110,17 @@ def recorded_traffic(kernel_hash, variant=False):
         return None
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -193,11 +204,13 @@ def percentile(xs, q):
 
 
 # ------------------------------------------------------------------ reference arm
-def cpu_oracle_sample(budget_s=12.0, max_pairs=8):
-    """The FP64 oracle, as it stands, on whole 1024^2 pairs of the workload: as many as
-    fit in about budget_s seconds (at least one). Returns (fields/s, pairs, seconds,
-    threads, (u, v) of the first pair) — the field is kept to report how far the GPU's
-    field of the same pair is from it."""
+def cpu_oracle_sample(budget_s=12.0, max_pairs=8, workloads=True):
+    """The CPU baseline: the FP64 oracle, as it stands, on whole 1024^2 pairs of the
+    workload: as many as fit in about budget_s seconds (at least one) on all host cores,
+    and one pair on one core. Also the oracle's fields the GPU fields are compared with:
+    the first pair (and the same pair on its FP16-rounded pyramid) and, with `workloads`,
+    one pair of the 2048^2 workload and the smallest pair of the mixed batch (those inputs
+    are rendered here and reused by the GPU legs)."""
     import oracle
     from paper_1306_2461_gb300 import synth
     oracle.build()
@@ -214,7 +227,21 @@ def cpu_oracle_sample(budget_s=12.0, max_pairs=8):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return done / dt, done, dt, oracle.threads(), first
+    nt = oracle.threads()
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.flow(pairs[0].I1, pairs[0].I2, LEVELS, RADIUS, ITERS)
+    single = time.perf_counter() - t1
+    oracle.set_threads(nt)
+    res = {"value": done / dt, "pairs": done, "secs": dt, "threads": nt, "first": first, "single_s": single,
+           "first_stored_f16": oracle.flow_stored(pairs[0].I1, pairs[0].I2, LEVELS, RADIUS, ITERS, "f16")}
+    if workloads:
+        c3 = synth.make_c3()
+        res["c3"] = (c3, oracle.flow(c3.I1, c3.I2, 4, 3, 6))
+        distinct = synth.make_batch(16, seed=3)
+        small = min(range(16), key=lambda i: distinct[i].I1.size)
+        res["c4"] = (distinct, small, oracle.flow(distinct[small].I1, distinct[small].I2, 3, 4, 5))
+    return res
 
 
 def run_reference(args, rank, world):
@@ -282,7 +309,7 @@ def main():
     # the CPU oracle runs before the first GPU call (no fork after CUDA init)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample()
+        cpu = cpu_oracle_sample(workloads=not args.no_extras and not args.i1grad)
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -350,7 +377,7 @@ def main():
 
     extras = {}
     if not args.no_extras and not args.i1grad:
-        extras = extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows, world)
+        extras = extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows, world, cpu)
 
     # accuracy of the timed configuration on one pair (outside the timed region)
     p0 = src[0]
@@ -428,24 +455,38 @@ def main():
         line["clocks"] = clocks
     line.update(extras)
     if cpu is not None:
-        val, npairs, secs, threads, (uo, vo) = cpu
-        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"{npairs} whole {H}x{W} pairs of the workload in {secs:.1f} s "
-                                          "(FP64 C oracle, OpenMP)"}
-        # the timed configuration's field of the first pair against the oracle's
+        uo, vo = cpu["first"]
+        us16, vs16 = cpu["first_stored_f16"]
+        line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["threads"], "kind": "oracle",
+                                "sample": f"{cpu['pairs']} whole {H}x{W} pairs of the workload in {cpu['secs']:.1f} s "
+                                          "(FP64 C oracle, OpenMP)",
+                                "single_thread": {"value": 1.0 / cpu["single_s"], "unit": UNIT, "cores": 1,
+                                                  "sample": f"one whole {H}x{W} pair in {cpu['single_s']:.1f} s"},
+                                "cpu_model": cpu_model()}
+        # the timed configuration's field of the first pair against the oracle's: over every
+        # interior pixel; over those whose FP64 result the FP16 rounding of the pyramid
+        # itself moves by less than half the tolerance (the others counted); and against
+        # the oracle run on the FP16-rounded pyramid (the implementation check)
         d = np.maximum(np.abs(u0 - uo), np.abs(v0 - vo))[m:-m, m:-m]
+        sens = (np.maximum(np.abs(us16 - uo), np.abs(vs16 - vo)) > 0.5 * 2e-2)[m:-m, m:-m]
+        dimpl = np.maximum(np.abs(u0 - us16), np.abs(v0 - vs16))[m:-m, m:-m]
         line["vs_oracle_px"] = {"max": float(d.max()), "rms": float(np.sqrt((d ** 2).mean())),
                                 "p99_9": float(np.percentile(d, 99.9)), "margin_px": m,
-                                "note": "FP16-storage batched field vs the FP64 oracle on the unrounded pyramid, "
-                                        "interior pixels (stated tolerance: 2e-2 max and 5e-3 RMS on the pixels the "
-                                        "storage rounding does not move; tests/helpers.py)"}
+                                "max_rounding_aware": float(d[~sens].max()), "storage_sensitive_px": int(sens.sum()),
+                                "compared_px": int(d.size),
+                                "max_vs_oracle_on_fp16_pyramid": float(dimpl.max()),
+                                "note": "FP16-storage batched field vs the FP64 oracle, interior pixels. max: every "
+                                        "pixel; max_rounding_aware: pixels whose FP64 result the FP16 rounding of the "
+                                        "pyramid moves by < 1e-2 px (the storage-sensitive ones counted); "
+                                        "max_vs_oracle_on_fp16_pyramid: against the oracle run on the rounded pyramid. "
+                                        "Stated tolerance 2e-2 max, 5e-3 RMS"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows, world=1):
+def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flows, world=1, cpu=None):
     """Outside the headline timed region: the plain FP32 single-pair form (the comparison
     the target names), the first-image-gradient variant, the batch at FP32 storage, e2e
     through the C ABI with host buffers (whole job over all ranks, like the headline),
@@ -567,7 +608,115 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
         ms, fields = aggregate(a.elapsed_time(b), B * Ke, world)
         out[key] = {"value": fields / (ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": world * B * 2 * H * W * 2,
                     "d2h_bytes_per_step": world * B * 2 * H * W * 4, "steps": Ke, "path": path}
-    out["serving"] = serving_leg(torch, synth)
+    out["serving"], out["serving_sweep"] = serving_leg(torch, synth)
+    out.update(workload_legs(torch, of, synth, stream, cpu))
+    out["table1_synthetic"] = table1_sweep(torch, of, synth, batch=16, reps=10)["table1_synthetic"]
+    return out
+
+
+def _epe(u, v, p, m):
+    e = np.sqrt((u - p.u_gt) ** 2 + (v - p.v_gt) ** 2)[m:-m, m:-m]
+    return {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}
+
+
+def workload_legs(torch, of, synth, stream, cpu=None, steps=10):
+    """The other workloads, batched and timed like the headline (graph replays, CUDA events),
+    each with its end-point error against the analytic field and its distance from the FP64
+    oracle on one pair:
+      c3: 2048^2 12-bit with a low-seeding band, band-limited flow up to 10 px; 4 levels, r = 3,
+          6 iterations, FP16 storage with FP64 solves on ill-conditioned pixels; 8 pairs per step
+          (one rendered pair, repeated);
+      c4: 64 pairs of mixed sizes (256^2, 512^2, 1024^2, 2048 x 1024 uint8, uniform + vortex flow);
+          3 levels, r = 4, 5 iterations, FP16 storage; 16 rendered pairs, cycled."""
+    from paper_1306_2461_gb300 import autotune
+    out = {}
+
+    def timed(flows, I1, I2, us, vs):
+        autotune.tune(flows, I1, I2, us, vs, stream=stream, reps=2, save=False)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                of.compute_batch(flows, I1, I2, us, vs, stream=stream)
+            stream.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                of.compute_batch(flows, I1, I2, us, vs, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+        return a.elapsed_time(b) / steps
+
+    dev16 = lambda a: torch.from_numpy(a.astype(np.int32)).cuda().to(torch.uint16)
+    # c3
+    have = cpu is not None and "c3" in cpu
+    p, (uo, vo) = cpu["c3"] if have else (synth.make_c3(), (None, None))
+    L3, r3, n3 = 4, 3, 6
+    plan = of.Plan.make(2048, 2048, L3, r3, n3, bits=12, storage="f16", fp64_cond=1e3)
+    B3 = 8
+    flows = [of.Flow(plan) for _ in range(B3)]
+    I1 = [dev16(p.I1)] * B3
+    I2 = [dev16(p.I2)] * B3
+    us = [torch.empty((2048, 2048), device="cuda") for _ in range(B3)]
+    vs = [torch.empty((2048, 2048), device="cuda") for _ in range(B3)]
+    ms = timed(flows, I1, I2, us, vs)
+    u = us[0].cpu().double().numpy()
+    v = vs[0].cpu().double().numpy()
+    m = (r3 + 2) * 2 ** (L3 - 1)
+    with of.Flow(plan) as f1:   # the batched field equals one of_compute of the pair
+        u1, v1 = f1.compute(I1[0], I2[0])
+        torch.cuda.synchronize()
+        same = bool(torch.equal(u1, us[0]) and torch.equal(v1, vs[0]))
+    leg = {"fields_per_s": B3 / (ms / 1000.0), "ms_per_step": ms, "pairs_per_step": B3,
+           "batched_equals_single_pair": same,
+           "mpix_iter_per_s": pixel_iterations(2048, 2048, L3, n3) * B3 / ms / 1000.0,
+           "epe_vs_ground_truth_px": _epe(u, v, p, m)}
+    if have:
+        reach = sum((r3 + 1) * n3 * 2 ** l for l in range(L3))
+        rows = np.arange(2048)
+        outside = (rows < 0.4 * 2048 - reach) | (rows >= 0.6 * 2048 + reach)
+        d = np.maximum(np.abs(u - uo), np.abs(v - vo))
+        dm, do = d[m:-m, m:-m], d[outside][:, m:-m]
+        leg["vs_oracle_px"] = {"max": float(dm.max()), "rms": float(np.sqrt((dm ** 2).mean())),
+                               "max_outside_band": float(do.max()), "rms_outside_band": float(np.sqrt((do ** 2).mean())),
+                               "p99_9_outside_band": float(np.percentile(do, 99.9)),
+                               "within_2e-2_outside_band": float((do <= 2e-2).mean()),
+                               "note": f"FP16 storage vs the unrounded FP64 oracle over every interior pixel (no "
+                                       f"exclusion of near-singular or unstable windows, which the parity tests count "
+                                       f"and leave out); the low-seeding band widened by {reach} px is where the "
+                                       f"method is chaotic"}
+    out["c3_2048_lowseed_f16_fp64"] = leg
+    for f in flows:
+        f.close()
+    del I1, I2, us, vs
+    # c4
+    have = cpu is not None and "c4" in cpu
+    if have:
+        distinct, small, (uo, vo) = cpu["c4"]
+    else:
+        distinct = synth.make_batch(16, seed=3)
+        small = min(range(16), key=lambda i: distinct[i].I1.size)
+    B4 = 64
+    pairs = [distinct[i % 16] for i in range(B4)]
+    plans = [of.Plan.make(*q.shape, 3, 4, 5, bits=8, storage="f16") for q in pairs]
+    flows = [of.Flow(pl) for pl in plans]
+    I1 = [torch.from_numpy(q.I1).cuda() for q in pairs]
+    I2 = [torch.from_numpy(q.I2).cuda() for q in pairs]
+    us = [torch.empty(q.shape, device="cuda") for q in pairs]
+    vs = [torch.empty(q.shape, device="cuda") for q in pairs]
+    ms = timed(flows, I1, I2, us, vs)
+    m = (4 + 2) * 4
+    epes = [_epe(us[i].cpu().double().numpy(), vs[i].cpu().double().numpy(), pairs[i], m)["rms"] for i in range(16)]
+    px = sum(q.I1.size for q in pairs)
+    leg = {"fields_per_s": B4 / (ms / 1000.0), "ms_per_step": ms, "pairs_per_step": B4,
+           "mpix_per_step": px / 1e6,
+           "epe_vs_ground_truth_px": {"rms_mean_over_pairs": float(np.mean(epes)), "rms_max_over_pairs": float(max(epes))}}
+    if have:
+        d = np.maximum(np.abs(us[small].cpu().double().numpy() - uo),
+                       np.abs(vs[small].cpu().double().numpy() - vo))[m:-m, m:-m]
+        leg["vs_oracle_px"] = {"pair_shape": list(pairs[small].I1.shape), "max": float(d.max()),
+                               "rms": float(np.sqrt((d ** 2).mean()))}
+    out["c4_mixed64_u8_f16"] = leg
+    for f in flows:
+        f.close()
     return out
 
 
@@ -628,30 +777,59 @@ def table1_sweep(torch, of, synth, batch=16, reps=20):
                                                  "batch": batch}}
 
 
-def serving_leg(torch, synth, rate_per_stream=125.0, warmup_s=0.25, measure_s=2.0, frames_per_stream=3):
-    """16 camera streams (8 x 512^2, 6 x 1024^2, 2 x 2048^2, 12-bit), Poisson arrivals
-    totalling 2000 frames/s, open loop; each stream's previous pyramid stays resident.
-    Latency = completion seen by the server's worker - scheduled arrival (includes the
-    host-to-device copy of the frame; no device-to-host copy of the field)."""
-    from paper_1306_2461_gb300 import serve
-    streams_cfg = synth.serving_streams(seed=4)
-    with serve.Server(levels=LEVELS, radius=RADIUS, iterations=ITERS, bits=BITS, storage="f16",
-                      hbm_budget_bytes=64 << 30, max_batch=64, max_inflight=2) as srv:
-        streams = []
-        for ps in streams_cfg:
-            frames = []
-            for _ in range(frames_per_stream):
-                frames.append(serve.pinned_frame(ps.frame()))
-                ps.advance()
-            streams.append((srv.open_stream(ps.H, ps.W), frames))
-        arrivals = synth.poisson_arrivals(len(streams), rate_per_stream, warmup_s + measure_s, seed=4)
-        results, _ = serve.run_open_loop(srv, streams, arrivals, warmup_s=warmup_s)
-        summ = serve.summarize(results, measure_s)
-        st = srv.stats()
-    summ.update({"streams": "8x512^2 + 6x1024^2 + 2x2048^2, 12-bit", "offered_frames_per_s": rate_per_stream * 16,
-                 "window_s": measure_s, "ticks": st["ticks"],
-                 "note": f"{frames_per_stream} rendered frames per stream, cycled; latency from scheduled arrival"})
-    return summ
+def serving_leg(torch, synth, rates=(2000.0, 4000.0, 6000.0, 8000.0), frames_per_stream=112, warm_frames=16):
+    """16 time-resolved camera streams (8 x 512^2, 6 x 1024^2, 2 x 2048^2, 12-bit; the 4:3:1
+    mix), each a sequence of consecutive frames of particles advected by RK4 through a
+    drifting vortex street (generated on the device, copied to pinned host memory: no frame
+    repeats), served with continuous batching and resident previous-frame pyramids under
+    open-loop Poisson arrivals, at each offered load in `rates` (pairs/s over all streams).
+    Every stream has exactly frames_per_stream arrivals; fields are counted from the
+    warm_frames-th arrival time until the first stream's last arrival. Latency = completion
+    seen by the server's worker - scheduled arrival (the host-to-device copy of the frame
+    included; no device-to-host copy of the field). EPE: one served pair per stream (frames
+    k, k+1 in the middle of the sequence) against the RK4 one-frame displacement."""
+    from paper_1306_2461_gb300 import serve, synth_gpu
+    n = sum(c for _, _, c in synth.SERVE_MIX)
+    kmid = frames_per_stream // 2
+    seqs = []
+    t_gen = time.perf_counter()
+    k = 0
+    for H, W, cnt in synth.SERVE_MIX:
+        for _ in range(cnt):
+            gs = synth_gpu.GpuParticleStream(H, W, seed=4 * 1009 + k)
+            frames, gts = synth_gpu.render_sequence(gs, frames_per_stream, gt_at={kmid})
+            seqs.append((H, W, frames, gts[kmid]))
+            k += 1
+    t_gen = time.perf_counter() - t_gen
+    m = (RADIUS + 2) * 2 ** (LEVELS - 1)
+    sweep = []
+    for ri, rate in enumerate(rates):
+        per = rate / n
+        with serve.Server(levels=LEVELS, radius=RADIUS, iterations=ITERS, bits=BITS, storage="f16",
+                          hbm_budget_bytes=64 << 30, max_batch=64, max_inflight=2) as srv:
+            streams = [(srv.open_stream(H, W), frames) for H, W, frames, _ in seqs]
+            arrivals, last = synth_gpu.per_stream_arrivals(n, frames_per_stream, per, seed=4 + ri)
+            warm = warm_frames / per
+            end = min(last)
+            results, _, kept = serve.run_open_loop(srv, streams, arrivals, warmup_s=warm, end_s=end,
+                                                   keep=[(s, kmid + 1) for s in range(n)])
+            summ = serve.summarize(results, end - warm)
+            st = srv.stats()
+        epe = {}
+        for s, (H, W, _, (ug, vg)) in enumerate(seqs):
+            if (s, kmid + 1) not in kept:
+                continue
+            u, v = kept[(s, kmid + 1)]
+            e = torch.sqrt((u - ug) ** 2 + (v - vg) ** 2)[m:-m, m:-m]
+            epe.setdefault(f"{H}x{W}", []).append(float(torch.sqrt((e ** 2).mean())))
+        summ.update({"offered_pairs_per_s": rate, "window_s": end - warm, "ticks": st["ticks"],
+                     "epe_rms_px": {k2: float(np.mean(v2)) for k2, v2 in epe.items()}})
+        sweep.append(summ)
+    head = dict(sweep[0])
+    head.update({"streams": "8x512^2 + 6x1024^2 + 2x2048^2, 12-bit, time-resolved (no frame repeats)",
+                 "frames_per_stream": frames_per_stream, "generation_s": t_gen,
+                 "note": "latency from the scheduled arrival; EPE of one served pair per stream vs the RK4 displacement"})
+    return head, sweep
 
 
 if __name__ == "__main__":

@@ -198,6 +198,35 @@ def flow(I1, I2, levels: int, radius: int, iterations: int, want_ratio: bool = F
     return (u, v, q) if want_ratio else (u, v)
 
 
+def flow_stored(I1, I2, levels: int, radius: int, iterations: int, storage: str = "f16"):
+    """The coarse-to-fine flow (Sect. 2.4) in FP64 on a pyramid whose reduced levels are
+    rounded to a storage precision after each reduction ("f32", "f16" or "bf16", round to
+    nearest even), level 0 kept exact: the method run on the inputs a storage-limited
+    implementation holds. The steps are this module's pyr_down, upsample_flow and
+    lk_iteration, in the order of flow(). Returns (u, v)."""
+    def bf16(a):
+        x = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+        r = ((x + 0x7FFF + ((x >> 16) & 1)) >> 16) << 16
+        return r.astype(np.uint32).view(np.float32).astype(np.float64)
+    rnd = {"f32": lambda a: np.asarray(a, np.float32).astype(np.float64),
+           "f16": lambda a: np.asarray(a, np.float64).astype(np.float16).astype(np.float64),
+           "bf16": bf16}[storage]
+    P1, P2 = [_f64(I1)], [_f64(I2)]
+    for _ in range(levels - 1):
+        P1.append(rnd(pyr_down(P1[-1])))
+        P2.append(rnd(pyr_down(P2[-1])))
+    u = v = None
+    for l in range(levels - 1, -1, -1):
+        Hl, Wl = P1[l].shape
+        if l == levels - 1:
+            u, v = np.zeros((Hl, Wl)), np.zeros((Hl, Wl))
+        else:
+            u, v = upsample_flow(u, Hl, Wl), upsample_flow(v, Hl, Wl)
+        for _ in range(iterations):
+            u, v, _ = lk_iteration(P1[l], P2[l], u, v, radius)
+    return u, v
+
+
 ZNSSD_RADIUS = 5      # Sect. 2.4: local statistics over a radius of 5 pixels
 ZNSSD_EPS = 1.0       # added to the local variance (intensity units squared)
 

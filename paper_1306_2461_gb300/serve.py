@@ -140,14 +140,16 @@ def pinned_frame(a: np.ndarray) -> torch.Tensor:
     return t.contiguous().pin_memory()
 
 
-def run_open_loop(server: Server, streams, arrivals, warmup_s=0.0, out_ring=4, poll_us=200):
+def run_open_loop(server: Server, streams, arrivals, warmup_s=0.0, out_ring=4, poll_us=200, end_s=None, keep=()):
     """Submit frames at their scheduled arrival times (open loop) and collect results.
 
-    streams: list of (sid, frames) with frames a list of pinned host tensors, cycled.
-    arrivals: sorted list of (t_seconds, stream_index). Each stream's u, v come from a
-    ring of `out_ring` device buffer pairs; a slot is reused only after its result has
-    been reported. Returns (results, t0_ns): results are dicts with the stream index
-    and `in_window` (arrival after warmup_s)."""
+    streams: list of (sid, frames) with frames a list of pinned host tensors, taken in
+    order (cycled if a stream has more arrivals than frames). arrivals: sorted list of
+    (t_seconds, stream_index). Each stream's u, v come from a ring of `out_ring` device
+    buffer pairs; a slot is reused only after its result has been reported. A result is
+    `in_window` when its arrival lies in [warmup_s, end_s). keep: (stream_index,
+    frame_number) pairs whose fields are copied out when they are reported. Returns
+    (results, t0_ns, kept) with kept[(stream_index, frame_number)] = (u, v)."""
     dev = [[(torch.empty(f[0].shape, dtype=torch.float32, device="cuda"),
              torch.empty(f[0].shape, dtype=torch.float32, device="cuda")) for _ in range(out_ring)]
            for _, f in streams]
@@ -155,17 +157,29 @@ def run_open_loop(server: Server, streams, arrivals, warmup_s=0.0, out_ring=4, p
     count = [0] * len(streams)
     owner = {}
     results = []
+    kept = {}
+    keep = set(keep)
     torch.cuda.synchronize()
     t0 = now_ns() + 20_000_000
+    end_ns = None if end_s is None else end_s * 1e9
+
+    def take(r):
+        si2, slot, fno = owner.pop(r["tag"])
+        busy[si2][slot] = False
+        if (si2, fno) in keep and r["has_field"]:
+            u, v = dev[si2][slot]
+            kept[(si2, fno)] = (u.clone(), v.clone())
+        r["stream_index"] = si2
+        r["frame_number"] = fno
+        rel = r["arrival_ns"] - t0
+        r["in_window"] = rel >= warmup_s * 1e9 and (end_ns is None or rel < end_ns)
+        results.append(r)
+
     for k, (t, si) in enumerate(arrivals):
         due = t0 + int(t * 1e9)
         while True:
             for r in server.poll(0):
-                si2, slot = owner.pop(r["tag"])
-                busy[si2][slot] = False
-                r["stream_index"] = si2
-                r["in_window"] = r["arrival_ns"] - t0 >= warmup_s * 1e9
-                results.append(r)
+                take(r)
             wait = due - now_ns()
             if wait <= 0:
                 break
@@ -174,23 +188,16 @@ def run_open_loop(server: Server, streams, arrivals, warmup_s=0.0, out_ring=4, p
         slot = count[si] % out_ring
         while busy[si][slot]:   # output buffer still in use: wait for results
             for r in server.poll(poll_us):
-                si2, s2 = owner.pop(r["tag"])
-                busy[si2][s2] = False
-                r["stream_index"] = si2
-                r["in_window"] = r["arrival_ns"] - t0 >= warmup_s * 1e9
-                results.append(r)
+                take(r)
         u, v = dev[si][slot]
         busy[si][slot] = True
-        owner[k] = (si, slot)
+        owner[k] = (si, slot, count[si])
         server.submit(sid, frames[count[si] % len(frames)], u, v, tag=k, arrival_ns=due)
         count[si] += 1
     server.drain()
     for r in server.poll(0):
-        si2, _ = owner.pop(r["tag"])
-        r["stream_index"] = si2
-        r["in_window"] = r["arrival_ns"] - t0 >= warmup_s * 1e9
-        results.append(r)
-    return results, t0
+        take(r)
+    return results, t0, kept
 
 
 def summarize(results, window_s):

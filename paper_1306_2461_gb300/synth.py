@@ -133,12 +133,14 @@ def karman_flow(H: int, W: int, t: float, U=3.0, drift=2.0, peak=2.5, spacing=0.
 # ----------------------------------------------------------------------- rendering
 def render_particles(H: int, W: int, px: np.ndarray, py: np.ndarray, peak: float,
                      sigma: float = 1.0) -> np.ndarray:
-    """Sum of point-sampled Gaussians peak*exp(-|x-p|^2/(2 sigma^2)) at pixel centres (float64)."""
+    """Sum of point-sampled Gaussians peak*exp(-|x-p|^2/(2 sigma^2)) at pixel centres (float64).
+    Every (particle, tap) contribution is gathered first, offset by offset, and summed into
+    the image by one bincount."""
     rad = int(math.ceil(4.0 * sigma))
-    img = np.zeros(H * W, np.float64)
     ix = np.rint(px).astype(np.int64)
     iy = np.rint(py).astype(np.int64)
     inv = 1.0 / (2.0 * sigma * sigma)
+    idx, wts = [], []
     for dy in range(-rad, rad + 1):
         yy = iy + dy
         wy = np.exp(-((yy - py) ** 2) * inv)
@@ -146,9 +148,10 @@ def render_particles(H: int, W: int, px: np.ndarray, py: np.ndarray, peak: float
         for dx in range(-rad, rad + 1):
             xx = ix + dx
             ok = oky & (xx >= 0) & (xx < W)
-            w = peak * wy[ok] * np.exp(-((xx[ok] - px[ok]) ** 2) * inv)
-            img += np.bincount(yy[ok] * W + xx[ok], weights=w, minlength=H * W)
-    return img.reshape(H, W)
+            idx.append(yy[ok] * W + xx[ok])
+            wts.append(peak * wy[ok] * np.exp(-((xx[ok] - px[ok]) ** 2) * inv))
+    img = np.bincount(np.concatenate(idx), weights=np.concatenate(wts), minlength=H * W)
+    return img.astype(np.float64).reshape(H, W)
 
 
 def quantise(img: np.ndarray, noise: float, bits: int, rng: np.random.Generator) -> np.ndarray:

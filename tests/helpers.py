@@ -8,8 +8,10 @@ Which pixels are compared (parity_check):
   - not within a decade of the singular guard at level 0 (a guard decision may flip);
   - not unstable: pixels whose FP64 result moves by more than a quarter of the
     tolerance when the input images are perturbed by 1 part in 10^6 (rounding-level
-    noise) or, with FP16/BF16 storage, when a few stored pyramid values round the other
-    way, are not determined to the tolerance by the method itself.
+    noise; a test may probe with a larger relative amplitude where the FP32 arithmetic's
+    accumulated rounding is larger, and says why) or, with FP16/BF16 storage, when a few
+    stored pyramid values round the other way, are not determined to the tolerance by
+    the method itself.
 Every exclusion is counted and bounded. The implementation check compares the CUDA
 path with the oracle run on the pyramid stored as the CUDA path stores it (level 0
 exact, reduced levels rounded to the storage type), so both sides see the same
@@ -116,7 +118,7 @@ def compare(u, v, uo, vo, mask=None):
 
 
 def parity_check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label="", margin=None, workload=True,
-                 excluded_max=None, sensitive_max=0.01, region=None, round0=False, probes=1, outliers_max=0.0,
+                 excluded_max=None, sensitive_max=0.01, region=None, round0=False, probes=1, probe_amp=1e-6,
                  i1grad=False):
     """Assert the tolerance of `storage` on the compared pixels (see the module docstring).
     workload=False (synthetic textures used for shape coverage) asserts the
@@ -145,35 +147,26 @@ def parity_check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label="", mar
     amb = ambiguous_mask(q, r, n) & ~border
     unstable = np.zeros((H, W), bool)
     us, vs_ = oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, round0=round0, i1grad=i1grad)
-    for k in range(probes):
+
+    def probe(k):
         rng = np.random.default_rng(12345 + k)
-        up, vp = oracle_mod.flow(I1 * (1 + rng.uniform(-1e-6, 1e-6, I1.shape)),
-                                 I2 * (1 + rng.uniform(-1e-6, 1e-6, I2.shape)), L, r, n, i1grad=i1grad)
-        unstable |= np.maximum(np.abs(up - uo), np.abs(vp - vo)) > 0.25 * tmax
+        up, vp = oracle_mod.flow(I1 * (1 + rng.uniform(-probe_amp, probe_amp, I1.shape)),
+                                 I2 * (1 + rng.uniform(-probe_amp, probe_amp, I2.shape)), L, r, n, i1grad=i1grad)
+        mv = np.maximum(np.abs(up - uo), np.abs(vp - vo)) > 0.25 * tmax
         if storage != "f32":
             # stability to a rounding flip of stored pyramid values
-            uq, vq = oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, perturb=1e-6, seed=7 + k,
+            uq, vq = oracle_flow_stored(oracle_mod, I1, I2, L, r, n, storage, perturb=probe_amp, seed=7 + k,
                                         round0=round0, i1grad=i1grad)
-            unstable |= np.maximum(np.abs(uq - us), np.abs(vq - vs_)) > 0.25 * tmax
+            mv |= np.maximum(np.abs(uq - us), np.abs(vq - vs_)) > 0.25 * tmax
+        return mv
+    for k in range(probes):
+        unstable |= probe(k)
     unstable &= ~border & ~amb
     invalid = border | amb | unstable
     limit = excluded_max if excluded_max is not None else (0.01 if workload else 0.05)
     assert amb.sum() + unstable.sum() <= limit * n_inner, \
         f"{int(amb.sum())} near-singular and {int(unstable.sum())} unstable of {n_inner} interior px"
-    dimpl = np.maximum(np.abs(u - us), np.abs(v - vs_))
-    dfull = np.maximum(np.abs(u - uo), np.abs(v - vo))
     sens = (np.maximum(np.abs(us - uo), np.abs(vs_ - vo)) > 0.5 * tmax) & ~invalid
-    if outliers_max > 0:
-        # chaotic pixels that none of the probes moved: counted, bounded, and left out
-        # of the max (their agreement is printed)
-        outl = ((dimpl > tmax) | ((dfull > tmax) & ~sens)) & ~invalid
-        n_out = int(outl.sum())
-        if n_out:
-            print(f"{label} {storage}: {n_out} compared px beyond tolerance "
-                  f"(max {max(dimpl[outl].max(), dfull[outl].max()):.3e})")
-        assert n_out <= outliers_max * max(1, int((~invalid).sum())), n_out
-        invalid = invalid | outl
-        sens &= ~outl
     impl = compare(u, v, us, vs_, invalid)
     st = compare(u, v, uo, vo, invalid)
     sm = compare(u, v, uo, vo, invalid | sens)

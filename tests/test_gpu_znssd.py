@@ -38,21 +38,36 @@ def test_level0_is_the_normalised_image(of, oracle_mod, storage, bits, atol, H, 
     assert np.abs(got - ref).max() <= atol
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_flow_with_normalisation_matches_oracle(of, oracle_mod, storage):
+@pytest.mark.parametrize("storage,atol,amp", [("f32", 2e-5, 1e-5), ("f16", 8e-3, 1e-6)])
+def test_flow_with_normalisation_matches_oracle(of, oracle_mod, storage, atol, amp):
     # particle images under uneven illumination (what the normalisation is for)
+    import torch
     p = synth.make_c2_uneven_light(512, 512, seed=3)
-    u, v = gpu_flow(p, 3, 4, 5, storage, flags=of.OF_FLAG_ZNSSD)
-    z1 = oracle_mod.znssd(p.I1.astype(np.float64))
-    z2 = oracle_mod.znssd(p.I2.astype(np.float64))
-    # Normalised particle images hold chaotic pixels (~0.1%) that each random 1e-6
-    # perturbation of the input finds anew; three probes exclude some, and up to 0.1% of
-    # the compared pixels may still differ beyond tolerance (counted and printed: 128 of
-    # 214k at FP32, at most 4.5e-3 px, when measured).
-    # With FP16, rounding the normalised level 0 moves ~2% of the pixels by more than
-    # half the tolerance even in exact arithmetic.
-    parity_check(u, v, (z1, z2), oracle_mod, 3, 4, 5, storage, f"znssd 512x512 {storage}", round0=True,
-                 probes=3, outliers_max=1e-3, sensitive_max=0.03)
+    plan = of.Plan.make(512, 512, 3, 4, 5, bits=12, storage=storage, flags=of.OF_FLAG_ZNSSD)
+    with of.Flow(plan) as f:
+        ut, vt = f.compute(to_dev(p.I1), to_dev(p.I2))
+        torch.cuda.synchronize()
+        assert f.sync_status() == of.OF_OK
+        g1 = f.get_level(0, 0).cpu().double().numpy()
+        g2 = f.get_level(1, 0).cpu().double().numpy()
+    u, v = ut.cpu().double().numpy(), vt.cpu().double().numpy()
+    # The normalisation (Eq. 2), per pixel: the device's level 0, at the storage type, against
+    # the oracle's FP64 normalisation of the camera images.
+    for g, I in ((g1, p.I1), (g2, p.I2)):
+        assert np.abs(g - oracle_mod.znssd(I.astype(np.float64))).max() <= atol
+    # The flow kernels on identical inputs: the oracle runs on the images the device
+    # normalised (its level 0 exactly; the reduced levels rounded to the storage type as
+    # the device stores them). Every compared pixel within the stated tolerance (no
+    # outlier allowance); near-singular and unstable windows are counted and left out as
+    # in every parity test. Normalisation turns particle-free windows into unit-variance
+    # noise whose windows the method determines poorly: there the FP64 result responds
+    # linearly to a perturbation of the images with a gain of ~250 px per unit relative
+    # change (2.5e-4 px at 1e-6, 6e-3 px at 1e-4, measured), and the rounding the FP32
+    # arithmetic accumulates over 15 iterations amounts to relative perturbations of a
+    # few 1e-6. At FP32 storage the stability probes therefore perturb by 1e-5; they leave
+    # out about 2% of the interior (bounded at 3%).
+    parity_check(u, v, (g1, g2), oracle_mod, 3, 4, 5, storage, f"znssd 512x512 {storage}", probes=3,
+                 probe_amp=amp, excluded_max=0.03, sensitive_max=0.03)
     rms, mx = epe(u, v, p, 24)     # normalising level 0 weakens the coarse levels: outliers
     print(f"EPE vs ground truth with normalisation: rms {rms:.4f} max {mx:.4f}")
 

@@ -40,21 +40,61 @@ def test_integer_translation_is_a_fixed_point_reached_exactly(oracle_mod):
     assert np.abs(valid(v, m) - d[1]).max() < 1e-6
 
 
+def _predicted_fixed_point_offset(T, H, W, d, r):
+    """First-order offset of the Gauss-Newton fixed point from a pure translation d:
+    with I1 = T and I2 = T(. - d), the iteration stops where the window sums of g r vanish
+    for r = I1 - bilinear(I2)(x + u); linearised around u = d, u*(m) - d = H_m^-1 sum_w g r
+    with r = T(x) - bilinear(I2)(x + d) (the interpolation residual, from the analytic
+    texture), g the central difference of bilinear samples of I2 at x + d +- (1, 0), (0, 1)
+    and H_m the window sum of g g^T. Written here with numpy and scipy's box filter, not
+    with the oracle's routines."""
+    from scipy import ndimage
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    I2 = T(xx - d[0], yy - d[1])
+
+    def bil(px, py):
+        px, py = np.clip(px, 0, W - 1), np.clip(py, 0, H - 1)
+        x0, y0 = np.floor(px).astype(int), np.floor(py).astype(int)
+        x1, y1 = np.minimum(x0 + 1, W - 1), np.minimum(y0 + 1, H - 1)
+        ax, ay = px - x0, py - y0
+        return (1 - ay) * ((1 - ax) * I2[y0, x0] + ax * I2[y0, x1]) + ay * ((1 - ax) * I2[y1, x0] + ax * I2[y1, x1])
+
+    X, Y = xx + d[0], yy + d[1]
+    res = T(xx, yy) - bil(X, Y)
+    gx = (bil(X + 1, Y) - bil(X - 1, Y)) / 2
+    gy = (bil(X, Y + 1) - bil(X, Y - 1)) / 2
+    k = 2 * r + 1
+
+    def box(a):
+        return ndimage.uniform_filter(a, size=k, mode="constant") * k * k
+    Sa, Sb, Sc, Sd, Se = box(gx * gx), box(gx * gy), box(gy * gy), box(gx * res), box(gy * res)
+    det = Sa * Sc - Sb * Sb
+    return (Sc * Sd - Sb * Se) / det, (Sa * Se - Sb * Sd) / det
+
+
 def test_subpixel_translation_recovered(oracle_mod):
     # Uniform (1.3, -0.7) px translation of a band-limited texture (frequencies
     # <= 1/16 cycles/px), window radius 10 as in Sect. 2.4. The recovered translation
-    # (mean and median over valid pixels) is within 0.01 px. Per pixel, bilinear
-    # interpolation leaves a residual ~ t(1-t)/2 * laplacian(T) (t = 0.3), which the
-    # window turns into a bias of order 0.21 * 2/(2r+1) ~ 0.02 px; bound it at 0.05.
+    # (mean and median over valid pixels) is within 0.01 px. Per pixel, the bilinear
+    # warp leaves an interpolation residual that moves the method's fixed point away from
+    # the true shift (by up to ~0.03 px here, and more with lower frequencies, where the
+    # windows are worse conditioned); that offset is predicted independently to first
+    # order, and every valid pixel's error must equal it within 0.01 px.
     d = (1.3, -0.7)
-    I1, I2 = synth.translated_texture_pair(128, 128, d, seed=1)
+    T = synth.band_limited_texture(seed=1)
+    yy, xx = np.mgrid[0:128, 0:128].astype(np.float64)
+    I1, I2 = T(xx, yy), T(xx - d[0], yy - d[1])
     L, r, n = 2, 10, 10
     u, v = oracle_mod.flow(I1, I2, L, r, n)
     m = (r + 2) * 2 ** (L - 1)
     eu, ev = valid(u, m) - d[0], valid(v, m) - d[1]
     assert abs(eu.mean()) < 0.01 and abs(ev.mean()) < 0.01
     assert np.median(np.maximum(np.abs(eu), np.abs(ev))) < 0.01
-    assert max(np.abs(eu).max(), np.abs(ev).max()) < 0.05
+    pu, pv = _predicted_fixed_point_offset(T, 128, 128, d, r)
+    resid = max(np.abs(eu - valid(pu, m)).max(), np.abs(ev - valid(pv, m)).max())
+    print(f"per-pixel error max {max(np.abs(eu).max(), np.abs(ev).max()):.4f} px, beyond the predicted "
+          f"interpolation offset {resid:.5f} px")
+    assert resid < 0.01
 
 
 def test_swapping_images_negates_flow(oracle_mod):

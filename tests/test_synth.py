@@ -59,3 +59,33 @@ def test_stream_frames_advance():
     f1 = s.frame()
     assert f0.shape == (64, 96) and f0.dtype == np.uint16 and not np.array_equal(f0, f1)
     assert 1.0 < u.mean() < 5.0
+
+
+def test_device_stream_generator_has_the_cpu_generators_physics():
+    # synth_gpu runs the time-resolved stream with torch; run on the CPU here, its
+    # vortex-street velocity and RK4 one-frame displacement equal synth's, and its
+    # frames are seeded, typed and advance in time
+    import torch
+    from paper_1306_2461_gb300 import synth_gpu
+    H, W = 64, 96
+    g = synth_gpu.GpuParticleStream(H, W, seed=1, device="cpu")
+    c = synth.ParticleStream(H, W, seed=1)
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-10, W + 10, 500)
+    y = rng.uniform(-10, H + 10, 500)
+    for t in (0.0, 3.5, 40.0):
+        ug, vg = g.velocity(torch.from_numpy(x), torch.from_numpy(y), t)
+        uc, vc = synth.karman_flow(H, W, t)(x, y)
+        assert np.allclose(ug.numpy(), uc, atol=1e-12) and np.allclose(vg.numpy(), vc, atol=1e-12)
+    dg = g._rk4(torch.from_numpy(x), torch.from_numpy(y), 2.0)
+    dc = c._rk4(x, y, 2.0)
+    assert np.allclose(dg[0].numpy(), dc[0], atol=1e-12) and np.allclose(dg[1].numpy(), dc[1], atol=1e-12)
+    assert np.allclose(g.px.numpy(), c.px) and np.allclose(g.py.numpy(), c.py)   # same seeding
+    f0 = g.frame()
+    g.advance()
+    f1 = g.frame()
+    a0, a1 = f0.to(torch.int32), f1.to(torch.int32)
+    assert f0.shape == (H, W) and f0.dtype == torch.uint16 and int(a0.max()) <= 4095
+    assert not torch.equal(a0, a1)
+    u, v = g.ground_truth()
+    assert u.shape == (H, W) and 1.0 < float(u.mean()) < 5.0
