@@ -177,8 +177,9 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  * Autotuning of the batched launch (of_compute_batch and the serving loop). Every
  * batch shape has the same results to within the stated tolerances whichever tuning
  * runs it; with grouped sums (generic_sums == 0) they are the results of of_compute bit
- * for bit (with the default tile height). Without a table entry a batch runs
- * {generic_sums 0, stage_i2 1, blocks_per_sm 0, phased 1, prefetch 0, tile_h 24, branches 1}.
+ * for bit (with the default tile height and fusion 1). Without a table entry a batch runs
+ * {generic_sums 0, stage_i2 1, blocks_per_sm 0, phased 1, prefetch 0, tile_h 24, branches 1,
+ * fusion 1}.
  * A tuning:
  *   generic_sums   1: per-output window sums of the run-time-radius kernel;
  *                  0: grouped sums of the kernel specialised for the radius
@@ -201,6 +202,12 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  *                  joined back into the caller's stream, inside the captured graph), so
  *                  that one group's launches fill the last waves of another's; 1 to 4
  *                  (0 means 1). Each pair's arithmetic is unchanged.
+ *   fusion         phase launches with grouped sums at the default tile height: 2 runs two
+ *                  consecutive iterations of a level (after its first) in one launch, each
+ *                  tile computing the first of them on its whole window region in shared
+ *                  memory (iteration fusion depth 2; fields equal to within the FP32
+ *                  tolerance, the reference flows of the region's pixels being the tile's);
+ *                  0 or 1: one iteration per launch
  *   ms             measured milliseconds per batch (of_autotune_batch output only)
  * The process-wide table is keyed by the method (in_format, storage, radius, levels,
  * iterations, OF_FLAG_ZNSSD, OF_FLAG_I1GRAD) and a size class, round(log2(mean level-0 pixels
@@ -214,6 +221,7 @@ typedef struct of_tuning {
     int32_t prefetch;
     int32_t tile_h;
     int32_t branches;
+    int32_t fusion;
     float ms;
 } of_tuning;
 

@@ -307,10 +307,15 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
             }
             if ((e = launch_phase_pyr(Q, first, p0.in_format, p0.storage, st)) != cudaSuccess) return e;
         }
-        // iterations, coarsest level first; flow buffers ping-pong
+        // iterations, coarsest level first; flow buffers ping-pong (one swap per launch). With
+        // fusion 2, iterations it and it + 1 of a level (it >= 1) run as one launch.
         const bool i1grad = (p0.flags & OF_FLAG_I1GRAD) != 0;
-        for (int k = 0; k < L * p0.iterations; ++k) {
-            const int l = L - 1 - k / p0.iterations, it = k % p0.iterations, cur = k & 1;
+        const bool fuse = t.fusion == 2 && !i1grad;
+        int cur = 0;
+        for (int k = 0; k < L * p0.iterations; ++k, cur = 1 - cur) {
+            const int l = L - 1 - k / p0.iterations, it = k % p0.iterations;
+            const bool two = fuse && it >= 1 && it + 1 < p0.iterations;   // iterations it, it + 1
+            const int last = two ? it + 1 : it;   // the iteration whose estimate this launch writes
             if (i1grad && it == 0) {
                 // the variant's window matrices of this level, from I1 alone
                 HessPhase Hp;
@@ -354,7 +359,7 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
                 } else {
                     a.mode = FLOW_SAME;
                 }
-                if (l == 0 && it == p0.iterations - 1) {
+                if (l == 0 && last == p0.iterations - 1) {
                     a.u_out = bp[i].u;
                     a.v_out = bp[i].v;
                 } else {
@@ -362,19 +367,22 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
                     a.fout_pitch = bp[i].pitch[l];
                 }
                 a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
-                const int th = i1grad ? I1_TH : tile_h;   // the variant's kernels have their own tile height
+                // the variant's kernels and the fused kernel have their own tile height
+                const int th = i1grad ? I1_TH : (two ? LK_TH : tile_h);
                 a.tiles = a.tiles_x * ((a.H + th - 1) / th);
                 a.status = bp[i].status;
-                a.stage_i2 = i1grad ? 0 : stage;
+                a.stage_i2 = (i1grad || two) ? 0 : stage;   // the fused kernel gathers
                 if (a.stage_i2) fill_stage_maps(a, I.m[i], level_elem(p0, l), p0.radius, tile_h);   // else gathered
                 a.hess = bp[i].hess;
                 a.hess_pitch = bp[i].pitch[l];
                 I.prefix[i + 1] = I.prefix[i] + a.tiles;
             }
             e = i1grad ? launch_phase_i1_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, st)
+                : two  ? launch_phase_iter2(I, level_elem(p0, l), p0.radius, p0.fp64_cond, st)
                        : launch_phase_iter(I, level_elem(p0, l), p0.radius, t.generic_sums != 0, p0.fp64_cond, tile_h,
                                            st);
             if (e != cudaSuccess) return e;
+            if (two) ++k;   // both iterations done
         }
     }
     return cudaSuccess;
@@ -478,7 +486,10 @@ static Tuning effective(const of_plan &p0, Tuning t)
         t.blocks_per_sm = 0;
         t.stage_i2 = 0;
         t.tile_h = 0;
+        t.fusion = 0;
     }
+    if (!t.phased || t.generic_sums || !radius_specialised(p0.radius) || (t.tile_h != 0 && t.tile_h != LK_TH))
+        t.fusion = 0;
     return t;
 }
 
@@ -600,7 +611,7 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
                               (int)(p0.iterations * 16 + (p0.flags & (OF_FLAG_GATHER | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD))),
                               hs[0]->device, t.generic_sums, t.stage_i2,
                               t.blocks_per_sm + 256 * t.phased + 65536 * t.prefetch + (1 << 24) * (t.tile_h != 0),
-                              t.phased ? t.branches : 0};
+                              t.phased ? t.branches + 16 * t.fusion : 0};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
 

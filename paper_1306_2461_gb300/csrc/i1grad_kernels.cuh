@@ -143,7 +143,7 @@ __device__ __forceinline__ void i1_iter_tile(const IterArgs &a, int tile, int r,
             if (in[k]) {
                 float c, gx, gy;
                 i1_grad<true>(I1, a.pitch, a.H, a.W, x, y, c, gx, gy);
-                const float Iw = bil<true>(I2, a.pitch, a.H, a.W, (float)x + f[k].x, (float)y + f[k].y);
+                const float Iw = bil_at<true>(I2, a.pitch, a.H, a.W, x, y, f[k].x, f[k].y);
                 const float e = resid(c, Iw, gx, gy, f[k].x - ref.x, f[k].y - ref.y);
                 p0 = gx * e;
                 p1 = gy * e;

@@ -119,6 +119,16 @@ cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool gen
     }
 }
 
+#define OF_CASE_PH2(R) \
+    case R: return phase2_launch<R>(P, elem, fp64_cond, s);
+cudaError_t launch_phase_iter2(const IterPhase &P, int elem, int radius, float fp64_cond, cudaStream_t s)
+{
+    switch (radius) {
+        OF_RADII(OF_CASE_PH2)
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 #define OF_CASE_PHH(R) \
     case R: return phase_hess_launch<R>(P, elem, radius, s);
 cudaError_t launch_phase_hess(const HessPhase &P, int elem, int radius, bool generic, cudaStream_t s)

@@ -79,6 +79,8 @@ struct Tuning {
     int prefetch = 0;        // phase launches: warm L2 for the tile this many blocks per SM ahead (0: off)
     int tile_h = 0;          // phase launches with grouped sums: iteration tile height (0: the default)
     int branches = 0;        // phase launches: concurrent launch sequences over parts of the batch (0: one)
+    int fusion = 0;          // phase launches: 2 fuses pairs of same-level iterations in one launch per tile
+                             // (fixed radii, default tile height); 0 or 1: one iteration per launch
 };
 // The tuning table entry for this method and size class, or the default.
 Tuning tuning_for(const of_plan &method, int size_class);

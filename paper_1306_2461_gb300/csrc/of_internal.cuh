@@ -210,6 +210,10 @@ cudaError_t launch_phase_pyr(const PyrPhase &P, bool first, int in_format, int s
 cudaError_t launch_phase_zn(const ZnPhase &P, int in_format, int storage, cudaStream_t s);
 cudaError_t launch_phase_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond, int tile_h,
                               cudaStream_t s);
+// Two same-level FLOW_SAME iterations in one launch per tile (fixed radii, tile height
+// LK_TH, taps gathered); the arguments are those of the second iteration's output and
+// the first's input.
+cudaError_t launch_phase_iter2(const IterPhase &P, int elem, int radius, float fp64_cond, cudaStream_t s);
 // The first-image-gradient variant: window matrices of one level, then its iterations.
 cudaError_t launch_phase_hess(const HessPhase &P, int elem, int radius, bool generic, cudaStream_t s);
 cudaError_t launch_phase_i1_iter(const IterPhase &P, int elem, int radius, bool generic, float fp64_cond,
@@ -247,5 +251,6 @@ template <int R> void *batch_kernel_ptr(int in_format, int storage);
 template <int R> cudaError_t radius_configure();
 template <int R> size_t radius_smem_bytes(int r, bool stage_i2);
 template <int R> bool radius_stage_maps(const IterArgs &a, StageMaps &m, int elem, int tile_h);
+template <int R> cudaError_t phase2_launch(const IterPhase &P, int elem, float fp64_cond, cudaStream_t s);
 
 }  // namespace of

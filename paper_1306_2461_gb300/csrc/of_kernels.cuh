@@ -306,31 +306,73 @@ __device__ __forceinline__ float2 lerp2(float2 p, float2 q, float2 t, float2 omt
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return add2(a, b); }
 
-// Bilinear sample with the position clamped to [0, W-1] x [0, H-1].
-template <bool NC, typename T>
-__device__ __forceinline__ float bil(const T *I, int pitch, int H, int W, float x, float y)
+// A sample position x + u is held as the integer x + floor(u) and the fraction
+// u - floor(u), which FP32 gives exactly for u >= 0 and within 2^-25 for u < 0: the
+// interpolation weights carry the flow's own precision rather than the rounding of the
+// sum x + u in FP32 (half an ulp of x + u, about 1.5e-5 px at a few hundred pixels). The integer part wraps around in 32 bits, so that a flow too
+// large for an int (floor(u) saturated) never passes a test for a range of the image or
+// of a staged window; where the result is clamped instead, floor(u) is first limited
+// to +-2^20 (the position is then far outside the image, on the same side).
+__device__ __forceinline__ int pos_floor(int x, float fu)
 {
-    x = fminf(fmaxf(x, 0.0f), (float)(W - 1));
-    y = fminf(fmaxf(y, 0.0f), (float)(H - 1));
-    const float fx = floorf(x), fy = floorf(y);
-    const int x0 = (int)fx, y0 = (int)fy;
+    return (int)((unsigned)x + (unsigned)__float2int_rz(fu));
+}
+__device__ __forceinline__ int pos_floor_clamped(int x, float fu)
+{
+    return x + max(min(__float2int_rz(fu), 1 << 20), -(1 << 20));
+}
+// The upper bound of (unsigned)(x0 - 1) for a position whose 4 x 4 tap footprint
+// (x0 - 1 .. x0 + 2) lies inside an extent of n pixels.
+__device__ __forceinline__ unsigned interior_span(int n) { return n > 3 ? (unsigned)(n - 3) : 0u; }
+
+// Bilinear sample at the position (x0 + ax, y0 + ay), ax, ay in [0, 1) (x0, y0 not
+// wrapped), clamped to [0, W-1] x [0, H-1], the right and bottom neighbours clamped.
+template <bool NC, typename T>
+__device__ __forceinline__ float bil(const T *I, int pitch, int H, int W, int x0, float ax, int y0, float ay)
+{
+    // a position left of 0 or at or right of W - 1 clamps to the end pixel, fraction 0
+    ax = (unsigned)x0 < (unsigned)(W - 1) ? ax : 0.0f;
+    ay = (unsigned)y0 < (unsigned)(H - 1) ? ay : 0.0f;
+    x0 = min(max(x0, 0), W - 1);
+    y0 = min(max(y0, 0), H - 1);
     const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
-    const float ax = x - fx, ay = y - fy;
     const T *r0 = I + (size_t)y0 * pitch, *r1 = I + (size_t)y1 * pitch;
     return lerpf(lerpf(ldf<NC>(r0 + x0), ldf<NC>(r0 + x1), ax), lerpf(ldf<NC>(r1 + x0), ldf<NC>(r1 + x1), ax), ay);
 }
 
-// I2 at p = (px, py) and its gradient at p: central difference of the bilinear samples
-// at p +- (1, 0) and p +- (0, 1). Away from the border the 12 distinct taps of the 4x4
-// neighbourhood are read once; near it each sample is clamped on its own.
+// I2 bilinear at (x + u, y + v), the position clamped to the image.
 template <bool NC, typename T>
-__device__ __forceinline__ void sample_grad(const T *I, int pitch, int H, int W, float px, float py,
+__device__ __forceinline__ float bil_at(const T *I, int pitch, int H, int W, int x, int y, float u, float v)
+{
+    const float fu = floorf(u), fv = floorf(v);
+    return bil<NC>(I, pitch, H, W, pos_floor_clamped(x, fu), u - fu, pos_floor_clamped(y, fv), v - fv);
+}
+
+// sample_grad by five clamped bilinear samples. Where no sample is clamped these are the
+// interior branch's interpolations in the same order, so the two agree bit for bit.
+template <bool NC, typename T>
+__device__ __forceinline__ void sample_grad_clamped(const T *I, int pitch, int H, int W, int x, int y, float u,
+                                                    float v, float &Iw, float &gx, float &gy)
+{
+    const float fu = floorf(u), fv = floorf(v);
+    const float ax = u - fu, ay = v - fv;
+    const int bx = pos_floor_clamped(x, fu), by = pos_floor_clamped(y, fv);
+    Iw = bil<NC>(I, pitch, H, W, bx, ax, by, ay);
+    gx = (bil<NC>(I, pitch, H, W, bx + 1, ax, by, ay) - bil<NC>(I, pitch, H, W, bx - 1, ax, by, ay)) * 0.5f;
+    gy = (bil<NC>(I, pitch, H, W, bx, ax, by + 1, ay) - bil<NC>(I, pitch, H, W, bx, ax, by - 1, ay)) * 0.5f;
+}
+
+// I2 at p = (x + u, y + v) and its gradient at p: central difference of the bilinear
+// samples at p +- (1, 0) and p +- (0, 1). Away from the border the 12 distinct taps of
+// the 4x4 neighbourhood are read once; near it each sample is clamped on its own.
+template <bool NC, typename T>
+__device__ __forceinline__ void sample_grad(const T *I, int pitch, int H, int W, int x, int y, float u, float v,
                                             float &Iw, float &gx, float &gy)
 {
-    if (px >= 1.0f && py >= 1.0f && px < (float)(W - 2) && py < (float)(H - 2)) {
-        const float fx = floorf(px), fy = floorf(py);
-        const int x0 = (int)fx, y0 = (int)fy;
-        const float ax = px - fx, ay = py - fy;
+    const float fu = floorf(u), fv = floorf(v);
+    const float ax = u - fu, ay = v - fv;
+    const int x0 = pos_floor(x, fu), y0 = pos_floor(y, fv);
+    if ((unsigned)x0 - 1u < interior_span(W) && (unsigned)y0 - 1u < interior_span(H)) {
         const int o = (y0 - 1) * pitch + x0;
         const T *rm = I + o, *r0 = I + (o + pitch), *r1 = I + (o + 2 * pitch), *r2 = I + (o + 3 * pitch);
         const float a0 = ldf<NC>(rm), a1 = ldf<NC>(rm + 1);
@@ -342,9 +384,7 @@ __device__ __forceinline__ void sample_grad(const T *I, int pitch, int H, int W,
         gx = (lerpf(lerpf(b1, b2, ax), lerpf(c1, c2, ax), ay) - lerpf(lerpf(bm, b0, ax), lerpf(cm, c0, ax), ay)) * 0.5f;
         gy = (lerpf(bot, lerpf(d0, d1, ax), ay) - lerpf(lerpf(a0, a1, ax), top, ay)) * 0.5f;
     } else {
-        Iw = bil<NC>(I, pitch, H, W, px, py);
-        gx = (bil<NC>(I, pitch, H, W, px + 1.0f, py) - bil<NC>(I, pitch, H, W, px - 1.0f, py)) * 0.5f;
-        gy = (bil<NC>(I, pitch, H, W, px, py + 1.0f) - bil<NC>(I, pitch, H, W, px, py - 1.0f)) * 0.5f;
+        sample_grad_clamped<NC>(I, pitch, H, W, x, y, u, v, Iw, gx, gy);
     }
 }
 
@@ -482,7 +522,7 @@ __device__ __forceinline__ void lk_tile_generic(const IterArgs &a, int tile, int
         if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
             const float2 f = flow_at<NC>(a, x, y);
             float Iw, gx, gy;
-            sample_grad<NC>(I2, a.pitch, a.H, a.W, (float)x + f.x, (float)y + f.y, Iw, gx, gy);
+            sample_grad<NC>(I2, a.pitch, a.H, a.W, x, y, f.x, f.y, Iw, gx, gy);
             const float e = resid(ldf<NC>(I1 + (size_t)y * a.pitch + x), Iw, gx, gy, f.x - ref.x, f.y - ref.y);
             p0 = gx * gx;
             p1 = gx * gy;
@@ -525,13 +565,13 @@ __device__ __forceinline__ void lk_tile_generic(const IterArgs &a, int tile, int
 // at multiples of 4 in image coordinates (tiles are multiples of 4 wide and high), so
 // the order of the additions depends only on the pixel's position, not on the tiling:
 // the batched and the per-pair launches give the same bits.
-template <int R, int TH = LK_TH> struct FixedTile {
+template <int R, int TH = LK_TH, int TW = LK_TW> struct FixedTile {
     static_assert(R >= 2, "the grouped box sums need 2R >= 4");
     static constexpr int W = 2 * R + 1;                // window width
     static constexpr int NV4 = (2 * R + 4 + 3) / 4;    // float4 loads for 4 outputs' windows
     static constexpr int RH = TH + 2 * R;              // region rows (tile + halo)
-    static constexpr int RW = LK_TW + 2 * R;           // region columns
-    static constexpr int RWP = LK_TW + 4 * NV4 - 4;    // padded row length (>= RW, multiple of 4)
+    static constexpr int RW = TW + 2 * R;              // region columns
+    static constexpr int RWP = TW + 4 * NV4 - 4;       // padded row length (>= RW, multiple of 4)
     static constexpr int PLANE = RH * RWP;
     static constexpr int NREG = RH * RW;               // region pixels
     static constexpr int PER = (NREG + LK_THREADS - 1) / LK_THREADS;   // region pixels per thread
@@ -544,7 +584,7 @@ template <int R, int TH = LK_TH> struct FixedTile {
     static constexpr int WIN_H = TH + 2 * R + 2 * STAGE_MARGIN + 4;
     static constexpr int win_w(int S)
     {
-        return (LK_TW + 2 * ((R + 1) / 2 * 2) + 2 * STAGE_MARGIN + 4 + 16 / S - 1 + 16 / S - 1) / (16 / S) * (16 / S);
+        return (TW + 2 * ((R + 1) / 2 * 2) + 2 * STAGE_MARGIN + 4 + 16 / S - 1 + 16 / S - 1) / (16 / S) * (16 / S);
     }
     static constexpr int win_bytes(int S) { return win_w(S) * WIN_H * S; }
     // Product planes of the iteration tile. Stage 1 computes pixel pairs (x, x+1) with x
@@ -557,9 +597,10 @@ template <int R, int TH = LK_TH> struct FixedTile {
     // of a quarter warp of the horizontal pass fall in distinct banks).
     static constexpr int RE = (R + 1) / 2 * 2;
     static constexpr int OFF = RE - R;
-    static constexpr int RWE = LK_TW + 2 * RE;
+    static constexpr int RWE = TW + 2 * RE;
     static constexpr int NVE = (OFF + 2 * R + 4 + 3) / 4;   // float4 column groups read per 4 outputs
-    static_assert(LK_TW - 4 + 4 * NVE <= RWE, "the horizontal pass reads computed columns only");
+    static_assert(TW % 4 == 0 && TW / 4 <= 32, "4-output groups, a row's groups in one warp");
+    static_assert(TW - 4 + 4 * NVE <= RWE, "the horizontal pass reads computed columns only");
     static constexpr int RWP1 = RWE;
     static constexpr int RWP2 = RWE + 2;
     static_assert(RWP1 % 4 == 0 && RWP2 % 4 == 2, "row lengths");
@@ -734,21 +775,21 @@ __device__ __forceinline__ void flow_pair(const IterArgs &a, int x, int y, bool 
     fq = q ? flow_mode<NC, MODE>(a, x + 1, y) : f2(0.0f, 0.0f);
 }
 
-__device__ __forceinline__ bool interior(float px, float py, int H, int W)
+// The 4 x 4 tap footprint of the position with integer part (x0, y0) lies inside the image.
+__device__ __forceinline__ bool interior(int x0, int y0, unsigned wspan, unsigned hspan)
 {
-    return px >= 1.0f && py >= 1.0f && px < (float)(W - 2) && py < (float)(H - 2);
+    return (unsigned)x0 - 1u < wspan && (unsigned)y0 - 1u < hspan;
 }
 
-// The interior branch of sample_grad for two sample positions at once (X, Y: their
-// coordinates), with every operation of the scalar form on both components. The 12 taps
-// of each come from the staged window (win: WW x WH elements, first element at image
-// (wx0, wy0)) when `inwin`, else from global memory. FX, FY: floor(X), floor(Y).
+// The interior branch of sample_grad for two sample positions at once (integer parts
+// (xp, yp) and (xq, yq), fractions AX, AY), with every operation of the scalar form on
+// both components. The 12 taps of each come from the staged window (win: WW x WH
+// elements, first element at image (wx0, wy0)) when `inwin`, else from global memory.
 template <bool NC, int WW, typename T>
 __device__ __forceinline__ void sample_grad2(const T *I, int pitch, const T *win, bool inwin, int cpx, int cpy,
-                                             int cqx, int cqy, float2 X, float2 Y, float2 FX, float2 FY, float2 &IW,
-                                             float2 &GX, float2 &GY)
+                                             int cqx, int cqy, int xp, int yp, int xq, int yq, float2 AX, float2 AY,
+                                             float2 &IW, float2 &GX, float2 &GY)
 {
-    const float2 AX = sub2(X, FX), AY = sub2(Y, FY);
     const float2 one = f2(1.0f, 1.0f);
     const float2 OX = sub2(one, AX), OY = sub2(one, AY);
     float2 A0, A1, BM, B0, B1, B2, CM, C0, C1, C2, D0, D1;
@@ -769,7 +810,6 @@ __device__ __forceinline__ void sample_grad2(const T *I, int pitch, const T *win
         D0 = f2(ldf<false>(p + 3 * WW), ldf<false>(q + 3 * WW));
         D1 = f2(ldf<false>(p + 3 * WW + 1), ldf<false>(q + 3 * WW + 1));
     } else {
-        const int xp = (int)FX.x, yp = (int)FY.x, xq = (int)FX.y, yq = (int)FY.y;
         const int op = (yp - 1) * pitch + xp, oq = (yq - 1) * pitch + xq;
         const T *mp = I + op, *mq = I + oq;
         const T *p0 = I + (op + pitch), *q0 = I + (oq + pitch);
@@ -811,84 +851,117 @@ __device__ __forceinline__ void box4v(const V *v, V o[4])
     o[3] = vadd(vadd(vadd(m, v[OFF + 2 * R + 1]), v[OFF + 2 * R + 2]), v[OFF + 2 * R + 3]);
 }
 
-// Horizontal pass of one pair plane, in place: row ry becomes, at columns 0..LK_TW-1,
-// the window sums of its outputs (two channels per float2). A warp takes two rows; a
-// quarter warp takes 4 groups of 4 outputs of each (with rows RWP2 = 2 mod 4 float2
-// long, its 16-byte reads hit distinct banks). Each row is read and rewritten by one warp.
-template <int R, int TH>
+// Horizontal pass of one pair plane, in place: row ry becomes, at columns 0..TW-1, the
+// window sums of its outputs (two channels per float2). For 64-wide tiles a warp takes
+// two rows and a quarter warp 4 groups of 4 outputs of each (with rows RWP2 = 2 mod 4
+// float2 long, its 16-byte reads hit distinct banks); other widths take one row per warp,
+// one group per lane. Each row is read and rewritten by one warp.
+template <int R, int TH, int TW = LK_TW>
 __device__ __forceinline__ void box_h_pairs(float2 *P)
 {
-    using F = FixedTile<R, TH>;
-    static_assert(LK_TW == 64 && LK_THREADS % 32 == 0, "a warp covers two rows of 16 groups");
-    constexpr int ROWP = F::RH / 2;
+    using F = FixedTile<R, TH, TW>;
+    static_assert(LK_THREADS % 32 == 0, "whole warps");
     constexpr int WARPS = LK_THREADS / 32;
     constexpr int RW4 = F::RWP2 / 2;   // float4 per row
     const int lane = threadIdx.x & 31;
-    const int rsub = (lane >> 2) & 1, g = ((lane >> 3) << 2) | (lane & 3);
+    constexpr bool TWO = TW == 64;
+    constexpr int NG = TW / 4;
+    const int rsub = TWO ? (lane >> 2) & 1 : 0, g = TWO ? (((lane >> 3) << 2) | (lane & 3)) : lane;
+    constexpr int ROWS = TWO ? F::RH / 2 : F::RH;   // warp-sized chunks
 #pragma unroll 1
-    for (int chunk = threadIdx.x >> 5; chunk < ROWP; chunk += WARPS) {
-        float4 *row = reinterpret_cast<float4 *>(P) + (2 * chunk + rsub) * RW4 + 2 * g;
-        float2 v[4 * F::NVE];
-#pragma unroll
-        for (int q = 0; q < 2 * F::NVE; ++q) {
-            const float4 t = row[q];
-            v[2 * q] = f2(t.x, t.y);
-            v[2 * q + 1] = f2(t.z, t.w);
-        }
+    for (int chunk = threadIdx.x >> 5; chunk < ROWS; chunk += WARPS) {
+        const bool act = TWO || g < NG;
+        float4 *row = reinterpret_cast<float4 *>(P) + ((TWO ? 2 * chunk + rsub : chunk) * RW4 + 2 * g);
         float2 o[4];
-        box4v<R, F::OFF>(v, o);
+        if (act) {
+            float2 v[4 * F::NVE];
+#pragma unroll
+            for (int q = 0; q < 2 * F::NVE; ++q) {
+                const float4 t = row[q];
+                v[2 * q] = f2(t.x, t.y);
+                v[2 * q + 1] = f2(t.z, t.w);
+            }
+            box4v<R, F::OFF>(v, o);
+        }
         __syncwarp();
-        row[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-        row[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+        if (act) {
+            row[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+            row[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+        }
     }
 }
 
-// Horizontal pass of the float plane P4, in place (16 items of a row in 16 lanes).
-template <int R, int TH>
+// Horizontal pass of the float plane P4, in place: for 64-wide tiles the 16 items of a
+// row in 16 lanes, else one row per warp.
+template <int R, int TH, int TW = LK_TW>
 __device__ __forceinline__ void box_h_single(float *P)
 {
-    using F = FixedTile<R, TH>;
-    constexpr int NG = LK_TW / 4;
-    constexpr int NITEMS = F::RH * NG;
-    constexpr int IT = (NITEMS + LK_THREADS - 1) / LK_THREADS;
-    float4 res[IT];
+    using F = FixedTile<R, TH, TW>;
+    constexpr int NG = TW / 4;
+    if constexpr (TW == LK_TW && NG == 16) {
+        constexpr int NITEMS = F::RH * NG;
+        constexpr int IT = (NITEMS + LK_THREADS - 1) / LK_THREADS;
+        float4 res[IT];
 #pragma unroll
-    for (int k = 0; k < IT; ++k) {
-        const int i = threadIdx.x + k * LK_THREADS;
-        if (i < NITEMS) {
-            const int ry = i / NG, g = i % NG;
-            const float4 *src = reinterpret_cast<const float4 *>(P + ry * F::RWP1 + 4 * g);
-            float v[4 * F::NVE];
+        for (int k = 0; k < IT; ++k) {
+            const int i = threadIdx.x + k * LK_THREADS;
+            if (i < NITEMS) {
+                const int ry = i / NG, g = i % NG;
+                const float4 *src = reinterpret_cast<const float4 *>(P + ry * F::RWP1 + 4 * g);
+                float v[4 * F::NVE];
 #pragma unroll
-            for (int q = 0; q < F::NVE; ++q) {
-                const float4 t = src[q];
-                v[4 * q] = t.x;
-                v[4 * q + 1] = t.y;
-                v[4 * q + 2] = t.z;
-                v[4 * q + 3] = t.w;
+                for (int q = 0; q < F::NVE; ++q) {
+                    const float4 t = src[q];
+                    v[4 * q] = t.x;
+                    v[4 * q + 1] = t.y;
+                    v[4 * q + 2] = t.z;
+                    v[4 * q + 3] = t.w;
+                }
+                float o[4];
+                box4v<R, F::OFF>(v, o);
+                res[k] = make_float4(o[0], o[1], o[2], o[3]);
             }
-            float o[4];
-            box4v<R, F::OFF>(v, o);
-            res[k] = make_float4(o[0], o[1], o[2], o[3]);
         }
-    }
-    __syncwarp();
+        __syncwarp();
 #pragma unroll
-    for (int k = 0; k < IT; ++k) {
-        const int i = threadIdx.x + k * LK_THREADS;
-        if (i < NITEMS) {
-            const int ry = i / NG, g = i % NG;
-            *reinterpret_cast<float4 *>(P + ry * F::RWP1 + 4 * g) = res[k];
+        for (int k = 0; k < IT; ++k) {
+            const int i = threadIdx.x + k * LK_THREADS;
+            if (i < NITEMS) {
+                const int ry = i / NG, g = i % NG;
+                *reinterpret_cast<float4 *>(P + ry * F::RWP1 + 4 * g) = res[k];
+            }
+        }
+    } else {
+        constexpr int WARPS = LK_THREADS / 32;
+        const int g = threadIdx.x & 31;
+#pragma unroll 1
+        for (int ry = threadIdx.x >> 5; ry < F::RH; ry += WARPS) {
+            float4 *row = reinterpret_cast<float4 *>(P + ry * F::RWP1 + 4 * g);
+            float o[4];
+            if (g < NG) {
+                float v[4 * F::NVE];
+#pragma unroll
+                for (int q = 0; q < F::NVE; ++q) {
+                    const float4 t = row[q];
+                    v[4 * q] = t.x;
+                    v[4 * q + 1] = t.y;
+                    v[4 * q + 2] = t.z;
+                    v[4 * q + 3] = t.w;
+                }
+                box4v<R, F::OFF>(v, o);
+            }
+            __syncwarp();
+            if (g < NG) row[0] = make_float4(o[0], o[1], o[2], o[3]);
         }
     }
 }
 
 // Vertical pass for the 4 outputs (rows 4g..4g+3, column tx): sums of the three planes.
-template <int R, int TH>
+template <int R, int TH, int TW = LK_TW>
 __device__ __forceinline__ void box_v_planes(const float2 *P01, const float2 *P23, const float *P4, int g, int tx,
                                              float2 s01[4], float2 s23[4], float s4[4])
 {
-    using F = FixedTile<R, TH>;
+    using F = FixedTile<R, TH, TW>;
     {
         float2 v[2 * R + 4];
 #pragma unroll
@@ -938,25 +1011,27 @@ __device__ __forceinline__ void stage1_pair(const IterArgs &a, int x, int y, flo
         flow_pair<NC, MODE>(a, x, y, inq, fp, fq);
     }
     const float2 i1 = ld_pair<NC>(I1 + (y * a.pitch + x), inq);
-    const float2 X = add2(f2((float)x, (float)(x + 1)), f2(fp.x, fq.x));
-    const float2 Y = add2(f2((float)y, (float)y), f2(fp.y, fq.y));
     float2 IW, GX, GY;
-    // Both pixels sample the interior (their 4x4 footprints inside the image) and, with a
-    // staged window, the footprints' corners (x0 - 1, y0 - 1) inside it. When the whole
-    // window lies inside the image, a footprint inside the window is inside the image,
-    // which is the interior condition, so only the window is tested.
-    const float2 FX = f2(floorf(X.x), floorf(X.y)), FY = f2(floorf(Y.x), floorf(Y.y));
-    const int cpx = (int)FX.x - 1 - wx0, cpy = (int)FY.x - 1 - wy0;
-    const int cqx = (int)FX.y - 1 - wx0, cqy = (int)FY.y - 1 - wy0;
+    // The positions' integer parts and fractions (exact; pos_floor). Both pixels sample
+    // the interior (their 4x4 footprints inside the image) and, with a staged window, the
+    // footprints' corners (x0 - 1, y0 - 1) inside it. When the whole window lies inside
+    // the image, a footprint inside the window is inside the image, which is the interior
+    // condition, so only the window is tested.
+    const float2 FU = f2(floorf(fp.x), floorf(fq.x)), FV = f2(floorf(fp.y), floorf(fq.y));
+    const float2 AX = sub2(f2(fp.x, fq.x), FU), AY = sub2(f2(fp.y, fq.y), FV);
+    const int xp = pos_floor(x, FU.x), yp = pos_floor(y, FV.x);
+    const int xq = pos_floor(x + 1, FU.y), yq = pos_floor(y, FV.y);
+    const int cpx = (int)((unsigned)xp - 1u - (unsigned)wx0), cpy = (int)((unsigned)yp - 1u - (unsigned)wy0);
+    const int cqx = (int)((unsigned)xq - 1u - (unsigned)wx0), cqy = (int)((unsigned)yq - 1u - (unsigned)wy0);
     const bool inwin = win && (unsigned)cpx < (unsigned)(WW - 3) && (unsigned)cqx < (unsigned)(WW - 3) &&
                        (unsigned)cpy < (unsigned)(WH - 3) && (unsigned)cqy < (unsigned)(WH - 3);
-    if (inq && (win_in_image ? inwin
-                             : (interior(X.x, Y.x, a.H, a.W) && interior(X.y, Y.y, a.H, a.W)))) {
-        sample_grad2<NC, WW>(I2, a.pitch, win, inwin, cpx, cpy, cqx, cqy, X, Y, FX, FY, IW, GX, GY);
+    const unsigned ws = interior_span(a.W), hs = interior_span(a.H);
+    if (inq && (win_in_image ? inwin : (interior(xp, yp, ws, hs) && interior(xq, yq, ws, hs)))) {
+        sample_grad2<NC, WW>(I2, a.pitch, win, inwin, cpx, cpy, cqx, cqy, xp, yp, xq, yq, AX, AY, IW, GX, GY);
     } else {
         float iw0, gx0, gy0, iw1 = 0.0f, gx1 = 0.0f, gy1 = 0.0f;
-        sample_grad<NC>(I2, a.pitch, a.H, a.W, X.x, Y.x, iw0, gx0, gy0);
-        if (inq) sample_grad<NC>(I2, a.pitch, a.H, a.W, X.y, Y.y, iw1, gx1, gy1);
+        sample_grad_clamped<NC>(I2, a.pitch, a.H, a.W, x, y, fp.x, fp.y, iw0, gx0, gy0);
+        if (inq) sample_grad_clamped<NC>(I2, a.pitch, a.H, a.W, x + 1, y, fq.x, fq.y, iw1, gx1, gy1);
         IW = f2(iw0, iw1);
         GX = f2(gx0, gx1);
         GY = f2(gy0, gy1);
@@ -1096,6 +1171,154 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
         }
     }
     return true;
+}
+
+// ------------------------------------------------ two iterations fused in one tile
+// Iterations k+1 and k+2 (same level, FLOW_SAME) of one 64 x TH output tile in one block,
+// the iteration fusion depth 2 of the batched launch. Step A computes iteration k+1 on the
+// tile's whole region (the RWE x RH pixels the tile's window sums read, rounded up to
+// whole 4-row groups) as a tile of that size of its own, from the estimate in global
+// memory, and keeps the result in shared memory (buffer FB, laid out like plane P01).
+// Step B computes iteration k+2 on the tile from FB. Each step takes its reference
+// flow at the tile's centre (step A from the estimate of iteration k, step B from FB's),
+// so the fused fields equal the unfused ones up to rounding (the region's pixels belong
+// to neighbouring tiles, whose references differ). The taps are gathered from global
+// memory; the region's rows are read twice as wide a halo as one iteration needs.
+template <int R, int TH> struct Fused2 {
+    using B = FixedTile<R, TH>;                        // step B: the tile
+    static constexpr int THA = (B::RH + 3) / 4 * 4;    // step A's output rows (B's region rows)
+    static constexpr int TWA = B::RWE;                 // step A's output columns (B's region columns)
+    using A = FixedTile<R, THA, TWA>;
+    static constexpr int FB_FLOATS = 2 * B::PAIR_PLANE;    // B::RH x B::RWP2 float2
+    static_assert(B::PLANES <= A::PLANES, "step B reuses step A's planes");
+    static constexpr int SMEM_FLOATS = A::PLANES + FB_FLOATS;
+};
+
+template <typename T, bool NC, int R, int TH>
+__device__ __forceinline__ void lk_tile_fused2(const IterArgs &a, int tile, float fp64_cond, float *smem)
+{
+    using X = Fused2<R, TH>;
+    using A = typename X::A;
+    using B = typename X::B;
+    float2 *P01 = reinterpret_cast<float2 *>(smem);
+    float2 *FB = reinterpret_cast<float2 *>(smem + A::PLANES);
+    const int tyi = tile / a.tiles_x;
+    const int ty0 = tyi * TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
+    const int ax0 = tx0 - B::RE, ay0 = ty0 - R;   // step A's output origin: B's region
+    const int cxr = min(tx0 + LK_TW / 2, a.W - 1), cyr = min(ty0 + TH / 2, a.H - 1);
+    // ---------------- step A: iteration k+1 on B's region, into FB
+    {
+        const float2 ref = flow_at_m<NC, FLOW_SAME>(a, cxr, cyr);
+        float2 *Q01 = P01;
+        float2 *Q23 = Q01 + A::PAIR_PLANE;
+        float *Q4 = reinterpret_cast<float *>(Q23 + A::PAIR_PLANE);
+        constexpr int NPR = A::RWE / 2, NPAIR = A::RH * NPR;
+        constexpr int DY = LK_THREADS / NPR, DX = LK_THREADS % NPR;
+        int ry = threadIdx.x / NPR, cx = threadIdx.x % NPR;
+        __syncthreads();
+#pragma unroll 1
+        for (int j = threadIdx.x; j < NPAIR; j += LK_THREADS) {
+            const int k2 = ry * (A::RWP2 / 2) + cx;
+            float4 s01, s23;
+            float2 s4;
+            stage1_pair<T, NC, FLOW_SAME, 1>(a, ax0 - A::RE + 2 * cx, ay0 - R + ry, ref, nullptr, nullptr, false, 0,
+                                             0, 0, s01, s23, s4);
+            reinterpret_cast<float4 *>(Q01)[k2] = s01;
+            reinterpret_cast<float4 *>(Q23)[k2] = s23;
+            reinterpret_cast<float2 *>(Q4)[ry * (A::RWP1 / 2) + cx] = s4;
+            ry += DY;
+            cx += DX;
+            if (cx >= NPR) {
+                cx -= NPR;
+                ++ry;
+            }
+        }
+        __syncthreads();
+        box_h_pairs<R, X::THA, X::TWA>(Q01);
+        box_h_pairs<R, X::THA, X::TWA>(Q23);
+        box_h_single<R, X::THA, X::TWA>(Q4);
+        __syncthreads();
+        constexpr int VITEMS = X::TWA * (X::THA / 4);
+#pragma unroll 1
+        for (int i = threadIdx.x; i < VITEMS; i += LK_THREADS) {
+            const int tx = i % X::TWA, g = i / X::TWA;
+            const int x = ax0 + tx;
+            float2 s01[4], s23[4];
+            float s4[4];
+            box_v_planes<R, X::THA, X::TWA>(Q01, Q23, Q4, g, tx, s01, s23, s4);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int ryb = 4 * g + jj, y = ay0 + ryb;
+                if (ryb >= B::RH) break;
+                float2 f = f2(0.0f, 0.0f);   // outside the image: never read by step B
+                if ((unsigned)x < (unsigned)a.W && (unsigned)y < (unsigned)a.H) {
+                    const float sj[5] = {s01[jj].x, s01[jj].y, s23[jj].x, s23[jj].y, s4[jj]};
+                    float xu, xv;
+                    f = solve2(sj, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv)
+                                                      : flow_at_m<NC, FLOW_SAME>(a, x, y);
+                }
+                FB[ryb * B::RWP2 + tx] = f;
+            }
+        }
+        __syncthreads();
+    }
+    // ---------------- step B: iteration k+2 on the tile, from FB
+    {
+        const float2 ref = FB[(cyr - ay0) * B::RWP2 + (cxr - ax0)];
+        float2 *P23 = P01 + B::PAIR_PLANE;
+        float *P4 = reinterpret_cast<float *>(P23 + B::PAIR_PLANE);
+        constexpr int NPR = B::RWE / 2, NPAIR = B::RH * NPR;
+        constexpr int DY = LK_THREADS / NPR, DX = LK_THREADS % NPR;
+        int ry = threadIdx.x / NPR, cx = threadIdx.x % NPR;
+#pragma unroll 1
+        for (int j = threadIdx.x; j < NPAIR; j += LK_THREADS) {
+            const int k2 = ry * (B::RWP2 / 2) + cx;
+            float4 s01, s23;
+            float2 s4;
+            stage1_pair<T, NC, FLOW_SAME, 1>(a, tx0 - B::RE + 2 * cx, ty0 - R + ry, ref,
+                                             reinterpret_cast<const float4 *>(FB) + k2, nullptr, false, 0, 0, 0, s01,
+                                             s23, s4);
+            reinterpret_cast<float4 *>(P01)[k2] = s01;
+            reinterpret_cast<float4 *>(P23)[k2] = s23;
+            reinterpret_cast<float2 *>(P4)[ry * (B::RWP1 / 2) + cx] = s4;
+            ry += DY;
+            cx += DX;
+            if (cx >= NPR) {
+                cx -= NPR;
+                ++ry;
+            }
+        }
+        __syncthreads();
+        box_h_pairs<R, TH>(P01);
+        box_h_pairs<R, TH>(P23);
+        box_h_single<R, TH>(P4);
+        __syncthreads();
+        constexpr int VITEMS = LK_TW * (TH / 4);
+#pragma unroll 1
+        for (int i = threadIdx.x; i < VITEMS; i += LK_THREADS) {
+            const int tx = i % LK_TW, g = i / LK_TW;
+            const int x = tx0 + tx;
+            if (x >= a.W || ty0 + 4 * g >= a.H) continue;
+            float2 s01[4], s23[4];
+            float s4[4];
+            box_v_planes<R, TH>(P01, P23, P4, g, tx, s01, s23, s4);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int y = ty0 + 4 * g + jj;
+                if (y >= a.H) break;
+                const float sj[5] = {s01[jj].x, s01[jj].y, s23[jj].x, s23[jj].y, s4[jj]};
+                float xu, xv;
+                const float2 f = solve2(sj, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv)
+                                                               : FB[(y - ay0) * B::RWP2 + (x - ax0)];
+                if (a.fout) {
+                    a.fout[(size_t)y * a.fout_pitch + x] = f;
+                } else {
+                    a.u_out[(size_t)y * a.W + x] = f.x;
+                    a.v_out[(size_t)y * a.W + x] = f.y;
+                }
+            }
+        }
+    }
 }
 
 // The iteration tile for radius R (0 = generic, radius r at run time). MODE: the flow

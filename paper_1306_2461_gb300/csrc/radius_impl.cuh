@@ -45,6 +45,29 @@ phase_iter_kernel(const __grid_constant__ IterPhase P, int r, float fp64_cond)
     lk_tile<T, true, R, MODE, TH>(P.a[p], &P.m[p], blockIdx.x - P.prefix[p], r, fp64_cond, smem, phase);
 }
 
+// Two same-level iterations of up to PHASE_PAIRS pairs in one launch (iteration fusion
+// depth 2): block b runs both on tile b - prefix[p] of pair p (tile height LK_TH).
+template <int R> constexpr int fused2_min_blocks()
+{
+    if constexpr (R == 0) {
+        return 1;
+    } else {
+        constexpr int b = 233472 / (4 * Fused2<R, LK_TH>::SMEM_FLOATS + 1024);
+        return b < 1 ? 1 : (b > 2 ? 2 : b);
+    }
+}
+template <typename T, int R>
+__global__ void __launch_bounds__(LK_THREADS, fused2_min_blocks<R>())
+phase_iter2_kernel(const __grid_constant__ IterPhase P, float fp64_cond)
+{
+    extern __shared__ __align__(128) float4 smem4[];
+    if constexpr (R != 0) {
+        const int p = phase_pair(P.prefix, P.npairs, blockIdx.x);
+        lk_tile_fused2<T, true, R, LK_TH>(P.a[p], blockIdx.x - P.prefix[p], fp64_cond,
+                                          reinterpret_cast<float *>(smem4));
+    }
+}
+
 // The window sums of five given planes, through the same passes as the iteration tile.
 template <int R>
 __global__ void __launch_bounds__(LK_THREADS)
@@ -191,6 +214,34 @@ cudaError_t phase_launch(const IterPhase &P, int elem, int r, float fp64_cond, i
     }
 }
 
+template <int R> size_t fused2_smem_bytes()
+{
+    if constexpr (R == 0) return 0;
+    else return sizeof(float) * (size_t)Fused2<R, LK_TH>::SMEM_FLOATS;
+}
+
+template <typename T, int R> static cudaError_t phase2_for(const IterPhase &P, float fp64_cond, cudaStream_t s)
+{
+    phase_iter2_kernel<T, R><<<P.prefix[P.npairs], LK_THREADS, fused2_smem_bytes<R>(), s>>>(P, fp64_cond);
+    return cudaGetLastError();
+}
+
+template <int R> cudaError_t phase2_launch(const IterPhase &P, int elem, float fp64_cond, cudaStream_t s)
+{
+    if constexpr (R == 0) {
+        return cudaErrorInvalidValue;   // fusion needs a fixed-radius kernel
+    } else {
+        if (P.prefix[P.npairs] == 0) return cudaSuccess;
+        switch (elem) {
+        case ET_U8: return phase2_for<uint8_t, R>(P, fp64_cond, s);
+        case ET_U16: return phase2_for<uint16_t, R>(P, fp64_cond, s);
+        case ET_F32: return phase2_for<float, R>(P, fp64_cond, s);
+        case ET_F16: return phase2_for<__half, R>(P, fp64_cond, s);
+        default: return phase2_for<__nv_bfloat16, R>(P, fp64_cond, s);
+        }
+    }
+}
+
 template <typename T, int R> static cudaError_t i1h_for(const HessArgs &a, int r, cudaStream_t s)
 {
     i1_hess_kernel<T, R><<<a.tiles, LK_THREADS, sizeof(float) * i1_smem_floats<R>(r, 3), s>>>(a, r);
@@ -331,6 +382,13 @@ template <int R> cudaError_t radius_configure()
 #undef OF_SET_ALT
     }
     OF_SET((window_sums_kernel<R>));
+    if constexpr (R != 0) {   // the fused two-iteration kernels
+        const int fb = (int)fused2_smem_bytes<R>();
+        for (const void *fn : {(const void *)phase_iter2_kernel<uint8_t, R>, (const void *)phase_iter2_kernel<uint16_t, R>,
+                               (const void *)phase_iter2_kernel<float, R>, (const void *)phase_iter2_kernel<__half, R>,
+                               (const void *)phase_iter2_kernel<__nv_bfloat16, R>})
+            if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, fb)) != cudaSuccess) return e;
+    }
     {
         const int r = R == 0 ? MAX_RADIUS : R;
         const int hb = (int)sizeof(float) * i1_smem_floats<R>(r, 3), ib = (int)sizeof(float) * i1_smem_floats<R>(r, 2);
@@ -366,6 +424,7 @@ template cudaError_t phase_i1_launch<OF_RADIUS>(const IterPhase &, int, int, flo
 template cudaError_t i1_launch<OF_RADIUS>(const IterArgs &, int, int, float, cudaStream_t);
 template void *batch_kernel_ptr<OF_RADIUS>(int, int);
 template bool radius_stage_maps<OF_RADIUS>(const IterArgs &, StageMaps &, int, int);
+template cudaError_t phase2_launch<OF_RADIUS>(const IterPhase &, int, float, cudaStream_t);
 template cudaError_t radius_configure<OF_RADIUS>();
 template size_t radius_smem_bytes<OF_RADIUS>(int, bool);
 

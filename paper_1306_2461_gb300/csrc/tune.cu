@@ -42,7 +42,8 @@ bool valid(const Tuning &t)
            t.blocks_per_sm <= 64 && t.phased >= 0 && t.phased <= 1 && !(t.generic_sums && t.stage_i2) &&
            !(t.phased && t.blocks_per_sm) && t.prefetch >= 0 && t.prefetch <= 16 &&
            (t.tile_h == 0 || t.tile_h == LK_TH || (t.tile_h == ALT_TH && t.phased && !t.generic_sums)) &&
-           t.branches >= 0 && t.branches <= 4 && (t.branches <= 1 || t.phased);
+           t.branches >= 0 && t.branches <= 4 && (t.branches <= 1 || t.phased) && t.fusion >= 0 && t.fusion <= 2 &&
+           (t.fusion <= 1 || (t.phased && !t.generic_sums && (t.tile_h == 0 || t.tile_h == LK_TH)));
 }
 
 void to_c(const Tuning &t, float ms, of_tuning *o)
@@ -54,6 +55,7 @@ void to_c(const Tuning &t, float ms, of_tuning *o)
     o->prefetch = t.prefetch;
     o->tile_h = t.tile_h ? t.tile_h : LK_TH;
     o->branches = t.branches ? t.branches : 1;
+    o->fusion = t.fusion ? t.fusion : 1;
     o->ms = ms;
 }
 
@@ -114,7 +116,9 @@ int of_tuning_set(const of_plan *method, int32_t size_class, const of_tuning *t)
     v.prefetch = t->prefetch;
     v.tile_h = t->tile_h == LK_TH ? 0 : t->tile_h;
     v.branches = t->branches == 1 ? 0 : t->branches;
+    v.fusion = t->fusion == 1 ? 0 : t->fusion;
     if (!valid(v)) return OF_EINVAL;
+    if (v.fusion == 2 && !radius_specialised(method->radius)) return OF_EINVAL;   // fixed-radius kernels only
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_table[key_of(*method, size_class)] = v;
     return OF_OK;
@@ -167,6 +171,15 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
                         cand.push_back(t);
                     }
                 }
+    // iteration fusion depth 2 (grouped sums, default tile height, phase launches), in one
+    // and in two concurrent sequences
+    if (radius_specialised(p0.radius) && !variant)
+        for (int nb = 1; nb <= (n > 1 ? 2 : 1); ++nb) {
+            Tuning t;
+            t.fusion = 2;
+            t.branches = nb > 1 ? nb : 0;
+            cand.push_back(t);
+        }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);

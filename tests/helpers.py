@@ -181,6 +181,7 @@ def parity_check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label="", mar
             assert sm["rms"] <= trms, sm
         assert sens.sum() <= sensitive_max * max(1, impl["n"]), int(sens.sum())
         assert sm["max"] <= tmax, sm
+    impl["invalid"] = invalid   # the pixels left out of the comparison (border, near-singular, unstable)
     return impl
 
 

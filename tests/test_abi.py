@@ -117,8 +117,20 @@ def test_tuning_table_host_calls(of):
         of.tuning_set(m, 20, branches=5)                                  # at most 4 concurrent sequences
     with pytest.raises(of.OfError):
         of.tuning_set(m, 20, branches=2, phased=0)                        # a phase-launch knob
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, fusion=3)                                    # fusion depth 1 or 2
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, fusion=2, tile_h=32)                         # at the default tile height
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, fusion=2, generic_sums=1, stage_i2=0)        # with the grouped sums
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, fusion=2, phased=0)                          # of the phase launches
+    with pytest.raises(of.OfError):
+        of.tuning_set(of.Plan.make(64, 64, 3, 7, 3, bits=12), 20, fusion=2)   # a fixed-radius kernel
+    of.tuning_set(m, 20, fusion=2)
+    assert of.tuning_get(m, 20)["fusion"] == 2
     of.tuning_set(m, 20, branches=3)
-    assert of.tuning_get(m, 20)["branches"] == 3
+    assert of.tuning_get(m, 20)["branches"] == 3 and of.tuning_get(m, 20)["fusion"] == 1
     of.tuning_set(m, 20, tile_h=32, prefetch=1)
     assert (of.tuning_get(m, 20)["tile_h"], of.tuning_get(m, 20)["prefetch"]) == (32, 1)
     v = of.Plan.make(64, 64, 3, 4, 5, bits=12, storage="f16", flags=of.OF_FLAG_I1GRAD)

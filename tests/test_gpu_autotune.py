@@ -43,18 +43,18 @@ def test_every_candidate_matches_the_per_pair_path(of, oracle_mod):
     torch.cuda.synchronize()
     best, cands = of.autotune_batch(flows, I1, I2, reps=2)
     print(best, cands)
-    assert len(cands) == 26 and best["ms"] == min(c["ms"] for c in cands)
-    assert sum(c["branches"] == 2 for c in cands) == 5
+    assert len(cands) == 28 and best["ms"] == min(c["ms"] for c in cands)
+    assert sum(c["branches"] == 2 for c in cands) == 6 and sum(c["fusion"] == 2 for c in cands) == 2
     sc = of.batch_size_class(flows)
     t = of.tuning_get(flows[0].plan, sc)
-    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches")
+    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches", "fusion")
     assert tuple(t[k] for k in keys) == tuple(best[k] for k in keys)
     for c in cands:
         of.tuning_set(flows[0].plan, sc, *(c[k] for k in keys))
         us, vs = of.compute_batch(flows, I1, I2)
         torch.cuda.synchronize()
         for k in range(len(sizes)):
-            if c["generic_sums"] == 0 and c["tile_h"] == 24:
+            if c["generic_sums"] == 0 and c["tile_h"] == 24 and c["fusion"] == 1:
                 assert torch.equal(us[k], ref[k][0]) and torch.equal(vs[k], ref[k][1]), (c, k)
             else:
                 m = 24
@@ -63,7 +63,7 @@ def test_every_candidate_matches_the_per_pair_path(of, oracle_mod):
                 assert d <= 1e-3, (c, k, d)
                 if k == 0:      # and the oracle's parity holds for these forms too
                     parity_check(us[k].cpu().double().numpy(), vs[k].cpu().double().numpy(), pairs[k],
-                                 oracle_mod, 3, 4, 3, "f32", f"generic sums {c['generic_sums']}, tile {c['tile_h']}")
+                                 oracle_mod, 3, 4, 3, "f32", f"generic sums {c['generic_sums']}, tile {c['tile_h']}, fusion {c['fusion']}")
     of.tuning_clear()
     for f in flows:
         f.close()
@@ -76,12 +76,12 @@ def test_cache_file_round_trip(of, tmp_path):
     path = str(tmp_path / "tune.json")
     ent = autotune.tune(flows, I1, I2, reps=1, path=path)
     sc = of.batch_size_class(flows)
-    assert ent["size_class"] == sc and len(ent["candidates"]) == 26
+    assert ent["size_class"] == sc and len(ent["candidates"]) == 28
     of.tuning_clear()
     assert of.tuning_get(flows[0].plan, sc) is None
     assert autotune.load(path) == 1
     t = of.tuning_get(flows[0].plan, sc)
-    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches")
+    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches", "fusion")
     assert tuple(t[k] for k in keys) == tuple(ent["best"][k] for k in keys)
     again = autotune.ensure(flows, I1, I2, path=path)      # known: no new timing
     assert again["candidates"] == [] and again["best"]["generic_sums"] == ent["best"]["generic_sums"]
@@ -125,6 +125,60 @@ def test_tall_tile_every_radius_ragged(of, oracle_mod, r):
     of.tuning_clear()
     for f in flows:
         f.close()
+
+
+@pytest.mark.parametrize("r", [2, 3, 4, 5, 6, 8, 10])
+def test_fused_iterations_every_radius_ragged(of, oracle_mod, r):
+    """Iteration fusion depth 2 (two same-level iterations per launch, the first computed
+    on each tile's whole window region in shared memory), on sizes with partial tiles,
+    three levels and 5 iterations (levels run 1 + 2 x 2 launches), FP32 and FP16
+    storage: within the storage's tolerance of the oracle, and of the unfused per-pair
+    path on the pixels the oracle's perturbation probe finds stable (fusion changes the
+    reference flow the first iteration's region pixels are rounded against, which an
+    unstable pixel amplifies like any other rounding change)."""
+    import torch
+    sizes = [(97, 130), (200, 333)]
+    pairs = [synth.make_c1(H, W, seed=60 + k) for k, (H, W) in enumerate(sizes)]
+    for storage in ("f32", "f16"):
+        tol = 1e-3 if storage == "f32" else 2e-2
+        amp = 1e-5 if storage == "f32" else 1e-6
+        flows = [of.Flow(of.Plan.make(H, W, 3, r, 5, bits=8, storage=storage)) for H, W in sizes]
+        I1 = [to_dev(p.I1) for p in pairs]
+        I2 = [to_dev(p.I2) for p in pairs]
+        ref = []
+        for k, (H, W) in enumerate(sizes):
+            with of.Flow(of.Plan.make(H, W, 3, r, 5, bits=8, storage=storage)) as f:
+                u, v = f.compute(I1[k], I2[k])
+                ref.append((u.clone(), v.clone()))
+        sc = of.batch_size_class(flows)
+        stable = [None, None]
+        for branches in (1, 2):
+            of.tuning_set(flows[0].plan, sc, fusion=2, branches=branches)
+            assert of.tuning_get(flows[0].plan, sc)["fusion"] == 2
+            us, vs = of.compute_batch(flows, I1, I2)
+            torch.cuda.synchronize()
+            for k in range(len(sizes)):
+                assert bool(torch.isfinite(us[k]).all()) and bool(torch.isfinite(vs[k]).all())
+                uf, vf = us[k].cpu().double().numpy(), vs[k].cpu().double().numpy()
+                if stable[k] is None:
+                    # 5 x 5 windows hold 0.75 particles on average at this density: with FP16
+                    # storage about 5% of their pixels move by more than a quarter of the
+                    # tolerance when one stored value's rounding flips (the probe), and about
+                    # 1.2% by more than half of it from the storage alone (oracle on the
+                    # stored pyramid against the unrounded one), so both caps are wider at r = 2
+                    res = parity_check(uf, vf, pairs[k], oracle_mod, 3, r, 5, storage,
+                                       f"fusion 2, r {r}, pair {k}", probe_amp=amp,
+                                       excluded_max=0.03 if r > 2 else 0.08,
+                                       sensitive_max=0.01 if r > 2 else 0.03)
+                    stable[k] = ~res["invalid"]
+                d = np.maximum(np.abs(uf - ref[k][0].cpu().double().numpy()),
+                               np.abs(vf - ref[k][1].cpu().double().numpy()))
+                print(f"fusion 2 r {r} {storage} branches {branches} pair {k}: vs unfused max {d[stable[k]].max():.3e} "
+                      f"on {int(stable[k].sum())} stable px, {d.max():.3e} on all")
+                assert d[stable[k]].max() <= tol, (r, storage, branches, k, float(d[stable[k]].max()))
+        of.tuning_clear()
+        for f in flows:
+            f.close()
 
 
 @pytest.mark.parametrize("branches", [2, 3, 4])
