@@ -75,6 +75,24 @@ __device__ __forceinline__ void prefetch_row(const void *base, int pitch, int el
     prefetch_l2(reinterpret_cast<const void *>(s), (uint32_t)(e - s));
 }
 
+// L1 prefetch of the 128-byte lines of the rectangle [y0, y1) x [x0, x1) of a pitched
+// image (elements of `elem` bytes), clamped to the image: line `slot` of at most `lpr`
+// per row (slot < (y1 - y0) lpr; a row's lines past its last column are skipped), so
+// that threads [0, (y1 - y0) lpr) take one line each.
+__device__ __forceinline__ void prefetch_lines_l1(const void *base, int pitch, int elem, int H, int W, int y0,
+                                                  int y1, int x0, int x1, int lpr, int slot)
+{
+    const int row = slot / lpr, line = slot - row * lpr;
+    const int y = y0 + row;
+    x0 = max(x0, 0);
+    x1 = min(x1, W);
+    if (x0 >= x1 || y < 0 || y >= min(y1, H)) return;
+    const char *r = static_cast<const char *>(base) + (size_t)y * pitch * elem;
+    const uintptr_t s = (reinterpret_cast<uintptr_t>(r + (size_t)x0 * elem) & ~uintptr_t(127)) + 128u * line;
+    if (s > reinterpret_cast<uintptr_t>(r + (size_t)(x1 - 1) * elem)) return;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(s));
+}
+
 // Warm L2 with what the block that runs iteration tile `tile` will read first: its region
 // (tile + r-pixel halo) of the current estimate (flow mode MODE, or a.mode at run time when
 // MODE < 0), of I1, of I2 widened by PF_MARGIN pixels for the displacement, and of the
@@ -624,8 +642,12 @@ template <int R, int TH = LK_TH, int TW = LK_TW> struct FixedTile {
         TH == LK_TH ? (R <= 6 ? OF_LK_MIN_BLOCKS : 2) : (SMEM_FIT < 1 ? 1 : (SMEM_FIT > 5 ? 5 : SMEM_FIT));
 };
 
+// Staged tile, while its boxes land: 0 no prefetch, 1 warm L2 with the region's I1 rows,
+// 2 bring the region's I1 lines (and, upsampling, the coarser estimate's) into L1. With 4
+// resident blocks per SM their lines (4.6 KB per 64 x 24 tile of 16-bit data) fit in what
+// the shared-memory carve-out leaves of L1; 2 measured 1.9% faster per batch step than 0.
 #ifndef OF_PREFETCH_I1
-#define OF_PREFETCH_I1 0   // staged tile: warm L2 with the region's I1 rows while its boxes land
+#define OF_PREFETCH_I1 2
 #endif
 constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's staging copies
 
@@ -1098,11 +1120,27 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
             if (SAME) tma_load_2d(P01, &maps->flow, tx0 - F::RE, ty0 - R, bar);
             tma_load_2d(win, &maps->i2, wx0, wy0, bar);
         }
-#if OF_PREFETCH_I1
+#if OF_PREFETCH_I1 == 1
         // while the boxes land: warm L2 with the region's rows of I1 (read by stage 1)
         if (threadIdx.x >= 32 && threadIdx.x < 32 + F::RH)
             prefetch_row(a.I1, a.pitch, S, a.H, a.W, ty0 - R, ty0 - R + F::RH, tx0 - F::RE, tx0 - F::RE + F::RWE,
                          threadIdx.x - 32);
+#elif OF_PREFETCH_I1 == 2
+        // while the boxes land: bring the region's lines of I1 (read by stage 1) into L1,
+        // and at the first iteration of a level those of the coarser estimate it upsamples
+        {
+            constexpr int LPR = (F::RWE * S + 127) / 128 + 1, N1 = F::RH * LPR;
+            constexpr int CRH = F::RH / 2 + 2, CLPR = ((F::RWE / 2 + 2) * 8 + 127) / 128 + 1;
+            constexpr int N = N1 + (MODE == FLOW_UPSAMPLE ? CRH * CLPR : 0);
+            for (int i = threadIdx.x; i < N; i += LK_THREADS) {
+                if (i < N1)
+                    prefetch_lines_l1(a.I1, a.pitch, S, a.H, a.W, ty0 - R, ty0 - R + F::RH, tx0 - F::RE,
+                                      tx0 - F::RE + F::RWE, LPR, i);
+                else
+                    prefetch_lines_l1(a.fin, a.fin_pitch, 8, a.Hc, a.Wc, (ty0 - R) >> 1, ((ty0 - R) >> 1) + CRH,
+                                      (tx0 - F::RE) >> 1, ((tx0 - F::RE) >> 1) + F::RWE / 2 + 2, CLPR, i - N1);
+            }
+        }
 #endif
         bool done = mbar_wait_bounded(bar, phase, STAGE_TIMEOUT_NS);
         if (__syncthreads_or(!done)) {
