@@ -425,7 +425,7 @@ def main():
                    "method": ("first-image-gradient variant (window matrix fixed per level)" if args.i1grad
                               else "second-image gradient at the displaced position"),
                    "tuning": ({k: tuning["best"][k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased",
-                                                               "prefetch", "tile_h", "branches", "fusion")}
+                                                               "prefetch", "tile_h", "branches", "fusion", "strip")}
                               if tuning else ("default (autotuner off)"
                                               if args.branches <= 1 and not args.tile_h and args.stage else
                                               f"forced (autotuner off): tile_h {args.tile_h or 'default'}, stage "
@@ -434,10 +434,10 @@ def main():
                        B * (of.workspace_bytes(plan16) + 4 * H * W) / 1e9),
                    "parallelism": f"replicas x{world}"},
         "autotune_candidates_ms": ([[c["generic_sums"], c["stage_i2"], c["blocks_per_sm"], c["phased"], c["prefetch"],
-                                     c["tile_h"], c["branches"], c["fusion"], round(c["ms"], 3)]
+                                     c["tile_h"], c["branches"], c["fusion"], c["strip"], round(c["ms"], 3)]
                                     for c in tuning["candidates"]] if tuning else None),
         "autotune_candidate_columns": ["generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h",
-                                       "branches", "fusion", "ms"],
+                                       "branches", "fusion", "strip", "ms"],
         "latency_ms": {"step_p50": percentile(step_ms, 50), "step_p99": percentile(step_ms, 99),
                        "step_max": max(step_ms)},
         "mpix_iter_per_s": pixel_iterations(H, W, LEVELS, ITERS) * value / 1e6,
@@ -566,7 +566,7 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
     out["batched_f32"] = {"fields_per_s": len(f32) * K32 / (a.elapsed_time(b) / 1000.0),
                           "ms_per_step": a.elapsed_time(b) / K32,
                           "tuning": ({k: t32[k] for k in ("generic_sums", "stage_i2", "blocks_per_sm", "phased",
-                                                          "prefetch", "tile_h", "branches", "fusion")} if t32 else None),
+                                                          "prefetch", "tile_h", "branches", "fusion", "strip")} if t32 else None),
                           "epe_vs_ground_truth_px": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())}}
     for f in f32:
         f.close()

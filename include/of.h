@@ -177,9 +177,9 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  * Autotuning of the batched launch (of_compute_batch and the serving loop). Every
  * batch shape has the same results to within the stated tolerances whichever tuning
  * runs it; with grouped sums (generic_sums == 0) they are the results of of_compute bit
- * for bit (with the default tile height and fusion 1). Without a table entry a batch runs
- * {generic_sums 0, stage_i2 1, blocks_per_sm 0, phased 1, prefetch 0, tile_h 24, branches 1,
- * fusion 1}.
+ * for bit (with the default tile height and fusion 1, whatever the strip). Without a table
+ * entry a batch runs {generic_sums 0, stage_i2 1, blocks_per_sm 0, phased 1, prefetch 0,
+ * tile_h 24, branches 1, fusion 1, strip 4}.
  * A tuning:
  *   generic_sums   1: per-output window sums of the run-time-radius kernel;
  *                  0: grouped sums of the kernel specialised for the radius
@@ -208,6 +208,11 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  *                  memory (iteration fusion depth 2; fields equal to within the FP32
  *                  tolerance, the reference flows of the region's pixels being the tile's);
  *                  0 or 1: one iteration per launch
+ *   strip          phase launches with grouped sums: tiles per block along a column of
+ *                  tiles, 1, 2 or 4 (0 means 4). The tiles of a group of 4 tile rows share
+ *                  one reference flow, so a block's tiles after the first take over the
+ *                  window sums of the rows they share with the tile above; the fields are
+ *                  the same bit for bit for every strip (of_compute runs strip 1)
  *   ms             measured milliseconds per batch (of_autotune_batch output only)
  * The process-wide table is keyed by the method (in_format, storage, radius, levels,
  * iterations, OF_FLAG_ZNSSD, OF_FLAG_I1GRAD) and a size class, round(log2(mean level-0 pixels
@@ -222,6 +227,7 @@ typedef struct of_tuning {
     int32_t tile_h;
     int32_t branches;
     int32_t fusion;
+    int32_t strip;
     float ms;
 } of_tuning;
 

@@ -73,7 +73,7 @@ def load(path: str | None = None) -> int:
         b = ent["best"]
         of.tuning_set(_plan_of(ent["method"]), ent["size_class"], b["generic_sums"], b["stage_i2"],
                       b["blocks_per_sm"], b.get("phased", 0), b.get("prefetch", 0), b.get("tile_h", 0),
-                      b.get("branches", 0), b.get("fusion", 1))
+                      b.get("branches", 0), b.get("fusion", 1), b.get("strip", 4))
     return len(data)
 
 

@@ -253,6 +253,8 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
     const int32_t prefetch_ahead = sms * t.prefetch;
     // iteration tile height: the tuned one for the grouped sums of a specialised radius
     const int tile_h = (t.tile_h == ALT_TH && !t.generic_sums && radius_specialised(p0.radius)) ? ALT_TH : LK_TH;
+    // tiles per block of the fixed-radius kernels (the run-time-radius kernel takes one)
+    const int strip = (!t.generic_sums && radius_specialised(p0.radius)) ? strip_len(tuning_strip(t)) : 1;
     cudaError_t e;
     for (int g0 = 0; g0 < n; g0 += PHASE_PAIRS) {
         const int m = n - g0 < PHASE_PAIRS ? n - g0 : PHASE_PAIRS;
@@ -369,7 +371,8 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
                 a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
                 // the variant's kernels and the fused kernel have their own tile height
                 const int th = i1grad ? I1_TH : (two ? LK_TH : tile_h);
-                a.tiles = a.tiles_x * ((a.H + th - 1) / th);
+                a.strip = (i1grad || two) ? 1 : strip;
+                a.tiles = strip_units(a.H, a.W, th, a.strip);
                 a.status = bp[i].status;
                 a.stage_i2 = (i1grad || two) ? 0 : stage;   // the fused kernel gathers
                 if (a.stage_i2) fill_stage_maps(a, I.m[i], level_elem(p0, l), p0.radius, tile_h);   // else gathered
@@ -611,7 +614,7 @@ int run_batch(int32_t n, const of_handle *hs, const void *const *I1s, const void
                               (int)(p0.iterations * 16 + (p0.flags & (OF_FLAG_GATHER | OF_FLAG_ZNSSD | OF_FLAG_I1GRAD))),
                               hs[0]->device, t.generic_sums, t.stage_i2,
                               t.blocks_per_sm + 256 * t.phased + 65536 * t.prefetch + (1 << 24) * (t.tile_h != 0),
-                              t.phased ? t.branches + 16 * t.fusion : 0};
+                              t.phased ? t.branches + 16 * t.fusion + 256 * tuning_strip(t) : 0};
         memcpy(k + pairs_bytes + prefix_bytes + sizeof(st), extra, sizeof(extra));
     }
 

@@ -192,10 +192,13 @@ __global__ void __launch_bounds__(LK_THREADS, batch_min_blocks<R>()) batch_kerne
                 }
                 a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
                 a.tiles = 0;
+                a.strip = 1;
                 a.status = bp.status;
                 a.stage_i2 = 0;   // no tensor maps: the TMA staging needs them in parameter space
-                if (l == 0 && !hd.znssd) live = lk_tile<Tin, false, R>(a, nullptr, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
-                else live = lk_tile<T, false, R>(a, nullptr, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
+                if (l == 0 && !hd.znssd)
+                    live = lk_tile<Tin, false, R, -1, LK_TH, false>(a, nullptr, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
+                else
+                    live = lk_tile<T, false, R, -1, LK_TH, false>(a, nullptr, j, hd.radius, hd.fp64_cond, smem, mbar_phase);
             }
         }
         if (phase + 1 < hd.nphases && !grid_barrier(hd, (unsigned int)(phase + 1) * gridDim.x)) return;

@@ -213,7 +213,8 @@ cudaError_t enqueue_pair(of_ctx *h, const void *I1, const void *I2, float *u, fl
             }
             a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
             const int th = i1grad ? I1_TH : LK_TH;   // the variant's kernels have their own tile height
-            a.tiles = a.tiles_x * ((a.H + th - 1) / th);
+            a.strip = 1;   // one tile per block: the most blocks for one pair
+            a.tiles = strip_units(a.H, a.W, th, a.strip);
             a.status = h->status;
             a.stage_i2 = !(p.flags & OF_FLAG_GATHER) && !i1grad ? 1 : 0;
             StageMaps maps;

@@ -81,7 +81,10 @@ struct Tuning {
     int branches = 0;        // phase launches: concurrent launch sequences over parts of the batch (0: one)
     int fusion = 0;          // phase launches: 2 fuses pairs of same-level iterations in one launch per tile
                              // (fixed radii, default tile height); 0 or 1: one iteration per launch
+    int strip = 0;           // phase launches with grouped sums: tiles per block along y (1, 2, 4; 0: 4)
 };
+// Tiles per block along y of a tuning's phase launches of grouped sums.
+inline int tuning_strip(const Tuning &t) { return t.strip ? t.strip : 4; }
 // The tuning table entry for this method and size class, or the default.
 Tuning tuning_for(const of_plan &method, int size_class);
 // round(log2(mean level-0 pixels per pair)) of a batch.

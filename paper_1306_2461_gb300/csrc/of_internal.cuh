@@ -78,7 +78,8 @@ struct IterArgs {
     int32_t fout_pitch;
     float *u_out, *v_out;    // final planes, pitch W (used when fout == NULL)
     int32_t tiles_x;         // tiles along x (for flattened work lists)
-    int32_t tiles;           // tiles in this level
+    int32_t tiles;           // work units in this level (tiles, or strips of `strip` tiles)
+    int32_t strip;           // fixed-radius tile: tiles per work unit along y (1, 2 or 4; others mean 1)
     int *status;             // the handle's device status word (errors only)
     int32_t stage_i2;        // stage the tile's I2 window (and, at FLOW_SAME, its estimate) in shared
                              // memory with the TMA copies of the launch's StageMaps (fixed-radius tile)
@@ -89,7 +90,7 @@ struct IterArgs {
 // Tensor maps of the staged iteration tile, passed as kernel parameters (TMA reads them
 // from parameter space).
 struct StageMaps {
-    CUtensorMap flow;        // fin (8-byte elements, W x H) in boxes of the tile's region (FLOW_SAME)
+    CUtensorMap flow;        // fin (8-byte elements, W x H) in boxes of rows of the tile's region (FLOW_SAME)
     CUtensorMap i2;          // I2 (storage type, W x H) in boxes of the tile's window
 };
 
@@ -162,6 +163,18 @@ static_assert(LK_TH % 4 == 0, "the vertical box pass takes 4 rows at a time");
 #endif
 constexpr int ALT_TH = OF_ALT_TH;
 static_assert(ALT_TH % 4 == 0 && ALT_TH != LK_TH, "a multiple of 4 other than LK_TH");
+// The fixed-radius iteration tile takes its reference flow per group of REF_GROUP tile
+// rows of a column of tiles, and a work unit is a strip of strip_len(strip) consecutive
+// tiles of one column inside one group (the tiles after the first take over the window
+// sums of the rows they share with the tile above).
+constexpr int REF_GROUP = 4;
+inline __host__ __device__ int strip_len(int strip) { return strip == 2 || strip == 4 ? strip : 1; }
+inline __host__ __device__ int strip_units(int H, int W, int tile_h, int strip)
+{
+    const int tx = (W + LK_TW - 1) / LK_TW, ty = (H + tile_h - 1) / tile_h, k = strip_len(strip);
+    return tx * ((ty + k - 1) / k);
+}
+
 // Output tile height of the first-image-gradient variant's kernels (two product planes,
 // so a taller tile still leaves room for many blocks per SM).
 #ifndef OF_I1_TH

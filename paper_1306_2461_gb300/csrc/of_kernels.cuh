@@ -102,8 +102,8 @@ constexpr int PF_MARGIN = 8;
 template <typename T, int MODE, int TH = LK_TH>
 __device__ __forceinline__ void prefetch_tile(const IterArgs &a, int tile, int r)
 {
-    const int tyi = tile / a.tiles_x;
-    const int ty0 = tyi * TH - r, tx0 = (tile - tyi * a.tiles_x) * LK_TW - r;
+    const int uy = tile / a.tiles_x;   // a work unit: its first tile
+    const int ty0 = uy * strip_len(a.strip) * TH - r, tx0 = (tile - uy * a.tiles_x) * LK_TW - r;
     const int ty1 = ty0 + TH + 2 * r, tx1 = tx0 + LK_TW + 2 * r;
     const int t = threadIdx.x;
     const int mode = MODE >= 0 ? MODE : a.mode;
@@ -630,8 +630,16 @@ template <int R, int TH = LK_TH, int TW = LK_TW> struct FixedTile {
     static constexpr int SMEM_NOSTAGE = OFF_WIN;              // launches without staging
     static constexpr int smem_staged(int S) { return OFF_WIN + (win_bytes(S) + 15) / 16 * 4; }
     static constexpr int SMEM_FLOATS = smem_staged(4);        // the largest (FP32 storage)
-    // the staged flow estimate is one TMA box of RWP2 x RH 8-byte elements written over P01
-    static constexpr int FLOW_BOX_BYTES = RWP2 * RH * 8;
+    // The staged flow estimate: TMA boxes of RWP2 x FLOW_BH 8-byte elements written over
+    // P01. Where row 2R (the first below the 2R rows a tile of a strip takes over from the
+    // tile above) starts on a 128-byte boundary (R a multiple of 4), boxes of 2R rows when
+    // they tile TH, so that every row of a region is staged (RH / 2R boxes for a strip's
+    // first tile, TH / 2R for the others), else one box of TH rows at row 2R; elsewhere one
+    // box of TH rows at row 0 for a strip's first tile, the other rows' estimates read from
+    // global memory.
+    static constexpr bool FLOW_BOX_BELOW = (2 * R * RWP2 * 8) % 128 == 0;
+    static constexpr int FLOW_BH = FLOW_BOX_BELOW && TH % (2 * R) == 0 ? 2 * R : TH;
+    static constexpr int FLOW_BOX_BYTES = RWP2 * FLOW_BH * 8;
 #ifndef OF_LK_MIN_BLOCKS
 #define OF_LK_MIN_BLOCKS 4   // resident blocks per SM the fixed-radius kernels are compiled for (R <= 6)
 #endif
@@ -873,13 +881,13 @@ __device__ __forceinline__ void box4v(const V *v, V o[4])
     o[3] = vadd(vadd(vadd(m, v[OFF + 2 * R + 1]), v[OFF + 2 * R + 2]), v[OFF + 2 * R + 3]);
 }
 
-// Horizontal pass of one pair plane, in place: row ry becomes, at columns 0..TW-1, the
-// window sums of its outputs (two channels per float2). For 64-wide tiles a warp takes
+// Horizontal pass of one pair plane, in place, over rows r0..RH-1: row ry becomes, at
+// columns 0..TW-1, the window sums of its outputs (two channels per float2). For 64-wide tiles a warp takes
 // two rows and a quarter warp 4 groups of 4 outputs of each (with rows RWP2 = 2 mod 4
 // float2 long, its 16-byte reads hit distinct banks); other widths take one row per warp,
 // one group per lane. Each row is read and rewritten by one warp.
 template <int R, int TH, int TW = LK_TW>
-__device__ __forceinline__ void box_h_pairs(float2 *P)
+__device__ __forceinline__ void box_h_pairs(float2 *P, int r0 = 0)
 {
     using F = FixedTile<R, TH, TW>;
     static_assert(LK_THREADS % 32 == 0, "whole warps");
@@ -889,11 +897,11 @@ __device__ __forceinline__ void box_h_pairs(float2 *P)
     constexpr bool TWO = TW == 64;
     constexpr int NG = TW / 4;
     const int rsub = TWO ? (lane >> 2) & 1 : 0, g = TWO ? (((lane >> 3) << 2) | (lane & 3)) : lane;
-    constexpr int ROWS = TWO ? F::RH / 2 : F::RH;   // warp-sized chunks
+    const int rows = TWO ? (F::RH - r0) / 2 : F::RH - r0;   // warp-sized chunks (r0, RH - r0 even)
 #pragma unroll 1
-    for (int chunk = threadIdx.x >> 5; chunk < ROWS; chunk += WARPS) {
+    for (int chunk = threadIdx.x >> 5; chunk < rows; chunk += WARPS) {
         const bool act = TWO || g < NG;
-        float4 *row = reinterpret_cast<float4 *>(P) + ((TWO ? 2 * chunk + rsub : chunk) * RW4 + 2 * g);
+        float4 *row = reinterpret_cast<float4 *>(P) + ((r0 + (TWO ? 2 * chunk + rsub : chunk)) * RW4 + 2 * g);
         float2 o[4];
         if (act) {
             float2 v[4 * F::NVE];
@@ -913,22 +921,22 @@ __device__ __forceinline__ void box_h_pairs(float2 *P)
     }
 }
 
-// Horizontal pass of the float plane P4, in place: for 64-wide tiles the 16 items of a
-// row in 16 lanes, else one row per warp.
+// Horizontal pass of the float plane P4, in place, over rows r0..RH-1: for 64-wide tiles
+// the 16 items of a row in 16 lanes, else one row per warp.
 template <int R, int TH, int TW = LK_TW>
-__device__ __forceinline__ void box_h_single(float *P)
+__device__ __forceinline__ void box_h_single(float *P, int r0 = 0)
 {
     using F = FixedTile<R, TH, TW>;
     constexpr int NG = TW / 4;
     if constexpr (TW == LK_TW && NG == 16) {
-        constexpr int NITEMS = F::RH * NG;
-        constexpr int IT = (NITEMS + LK_THREADS - 1) / LK_THREADS;
+        constexpr int IT = (F::RH * NG + LK_THREADS - 1) / LK_THREADS;
+        const int nitems = (F::RH - r0) * NG;
         float4 res[IT];
 #pragma unroll
         for (int k = 0; k < IT; ++k) {
             const int i = threadIdx.x + k * LK_THREADS;
-            if (i < NITEMS) {
-                const int ry = i / NG, g = i % NG;
+            if (i < nitems) {
+                const int ry = r0 + i / NG, g = i % NG;
                 const float4 *src = reinterpret_cast<const float4 *>(P + ry * F::RWP1 + 4 * g);
                 float v[4 * F::NVE];
 #pragma unroll
@@ -948,8 +956,8 @@ __device__ __forceinline__ void box_h_single(float *P)
 #pragma unroll
         for (int k = 0; k < IT; ++k) {
             const int i = threadIdx.x + k * LK_THREADS;
-            if (i < NITEMS) {
-                const int ry = i / NG, g = i % NG;
+            if (i < nitems) {
+                const int ry = r0 + i / NG, g = i % NG;
                 *reinterpret_cast<float4 *>(P + ry * F::RWP1 + 4 * g) = res[k];
             }
         }
@@ -957,7 +965,7 @@ __device__ __forceinline__ void box_h_single(float *P)
         constexpr int WARPS = LK_THREADS / 32;
         const int g = threadIdx.x & 31;
 #pragma unroll 1
-        for (int ry = threadIdx.x >> 5; ry < F::RH; ry += WARPS) {
+        for (int ry = r0 + (threadIdx.x >> 5); ry < F::RH; ry += WARPS) {
             float4 *row = reinterpret_cast<float4 *>(P + ry * F::RWP1 + 4 * g);
             float o[4];
             if (g < NG) {
@@ -1082,23 +1090,18 @@ template <int R, int TH = LK_TH> __device__ __forceinline__ void lk_tile_init(fl
     __syncthreads();
 }
 
-// Returns false if the staging copy did not complete in time (then OF_ETIMEOUT is in
-// *a.status, nothing of the tile was written, and the block must stop).
-template <typename T, bool NC, int R, int MODE, int TH = LK_TH>
-__device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps *maps, int tile, float fp64_cond,
-                                              float *smem, uint32_t &phase)
+// One tile of a work unit (lk_tile_fixed). A tile after the first of its strip takes over
+// region rows 0..2R-1 from the tile above; CM = 0: a first tile, 1: a later one, 2: as
+// `carry_rt` says at run time (one body for both, the loop of a strip). Returns false if
+// a staging copy did not complete in time.
+template <typename T, bool NC, int R, int MODE, int TH, int CM>
+__device__ __forceinline__ bool lk_tile_step(const IterArgs &a, const StageMaps *maps, int tx0, int ty0, float2 ref,
+                                             float fp64_cond, float *smem, uint32_t &phase, bool carry_rt)
 {
+    const bool CARRY = CM == 2 ? carry_rt : CM == 1;
     using F = FixedTile<R, TH>;
     unsigned char *win = reinterpret_cast<unsigned char *>(smem + F::OFF_WIN);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + F::OFF_BAR);
-    const int tyi = tile / a.tiles_x;
-    const int ty0 = tyi * TH, tx0 = (tile - tyi * a.tiles_x) * LK_TW;
-    const float2 ref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + TH / 2, a.H - 1));
-    __syncthreads();   // the previous tile's readers of smem are done
-    // Staging (a.stage_i2): one TMA box of I2, the tile's window displaced by the rounded
-    // reference flow, and at FLOW_SAME one box of the current estimate over the tile's
-    // region, written over plane P01: stage 1 reads each pair's estimate there before
-    // storing the pair's products in the same place.
     constexpr int S = (int)sizeof(T);
     constexpr int WW = F::win_w(S);
     constexpr bool SAME = MODE == FLOW_SAME;
@@ -1106,39 +1109,77 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
     float2 *P23 = P01 + F::PAIR_PLANE;
     float *P4 = reinterpret_cast<float *>(P23 + F::PAIR_PLANE);
     const bool staged = maps && a.stage_i2 != 0;
+    const int r0 = CARRY ? 2 * R : 0;   // the first region row this tile computes
+    __syncthreads();   // the previous tile's readers of smem are done
+    if (CARRY) {
+        // region rows TH .. TH+2R-1 of the tile above are rows 0 .. 2R-1 of this one:
+        // their window sums along x (columns 0..TW-1 of each plane) move up
+        constexpr int Q2 = LK_TW / 2, Q1 = LK_TW / 4;   // float4 per row: pair planes, P4
+        constexpr int N = 2 * R * (2 * Q2 + Q1);
+        for (int i = threadIdx.x; i < N; i += LK_THREADS) {
+            const int row = i / (2 * Q2 + Q1), c = i - row * (2 * Q2 + Q1);
+            float4 *dst, *src;
+            if (c < 2 * Q2) {
+                float2 *P = c < Q2 ? P01 : P23;
+                const int q = c < Q2 ? c : c - Q2;
+                dst = reinterpret_cast<float4 *>(P + row * F::RWP2) + q;
+                src = reinterpret_cast<float4 *>(P + (row + TH) * F::RWP2) + q;
+            } else {
+                dst = reinterpret_cast<float4 *>(P4 + row * F::RWP1) + (c - 2 * Q2);
+                src = reinterpret_cast<float4 *>(P4 + (row + TH) * F::RWP1) + (c - 2 * Q2);
+            }
+            *dst = *src;
+        }
+        __syncthreads();
+    }
+    // Staging (a.stage_i2): one TMA box of I2, the tile's window displaced by the
+    // rounded estimate at the tile's centre, and at FLOW_SAME the boxes of the current
+    // estimate over the rows this tile computes (FixedTile::FLOW_BH), written over plane
+    // P01: stage 1 reads each pair's estimate there before storing the pair's products
+    // in the same place (the estimates of rows no box covers are read from global memory).
+    const bool box = SAME && staged && (!CARRY || F::FLOW_BOX_BELOW);
+    constexpr bool ALL = F::FLOW_BH == 2 * R;   // boxes cover a first tile's whole region
+    const int bx0 = CARRY ? 2 * R : 0;          // first row of the boxes; rows below brow_end read them
+    const int nbox = !box ? 0 : (CARRY ? TH / F::FLOW_BH : (ALL ? F::RH / F::FLOW_BH : 1));
+    const int brow_end = box ? ((CARRY || ALL) ? F::RH : TH) : 0;
     int wx0 = 0, wy0 = 0;
     if (staged) {
         constexpr int E = 16 / S;
-        const int ox = __float2int_rn(fminf(fmaxf(ref.x, -(float)a.W), (float)a.W));
-        const int oy = __float2int_rn(fminf(fmaxf(ref.y, -(float)a.H), (float)a.H));
+        const float2 wref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + TH / 2, a.H - 1));
+        const int ox = __float2int_rn(fminf(fmaxf(wref.x, -(float)a.W), (float)a.W));
+        const int oy = __float2int_rn(fminf(fmaxf(wref.y, -(float)a.H), (float)a.H));
         const int wx = tx0 - F::RE + ox - F::STAGE_MARGIN - 2;
         wx0 = (wx >= 0 ? wx / E : -((-wx + E - 1) / E)) * E;   // a multiple of 16 bytes
         wy0 = ty0 - R + oy - F::STAGE_MARGIN - 2;
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, (uint32_t)(F::win_bytes(S) + (SAME ? F::FLOW_BOX_BYTES : 0)));
-            if (SAME) tma_load_2d(P01, &maps->flow, tx0 - F::RE, ty0 - R, bar);
+            mbar_arrive_expect_tx(bar, (uint32_t)(F::win_bytes(S) + nbox * F::FLOW_BOX_BYTES));
+            for (int b = 0; b < nbox; ++b)
+                tma_load_2d(P01 + (bx0 + b * F::FLOW_BH) * F::RWP2, &maps->flow, tx0 - F::RE,
+                            ty0 - R + bx0 + b * F::FLOW_BH, bar);
             tma_load_2d(win, &maps->i2, wx0, wy0, bar);
         }
 #if OF_PREFETCH_I1 == 1
         // while the boxes land: warm L2 with the region's rows of I1 (read by stage 1)
-        if (threadIdx.x >= 32 && threadIdx.x < 32 + F::RH)
-            prefetch_row(a.I1, a.pitch, S, a.H, a.W, ty0 - R, ty0 - R + F::RH, tx0 - F::RE, tx0 - F::RE + F::RWE,
-                         threadIdx.x - 32);
+        if (threadIdx.x >= 32 && threadIdx.x < 32 + F::RH - r0)
+            prefetch_row(a.I1, a.pitch, S, a.H, a.W, ty0 - R + r0, ty0 - R + F::RH, tx0 - F::RE,
+                         tx0 - F::RE + F::RWE, threadIdx.x - 32);
 #elif OF_PREFETCH_I1 == 2
-        // while the boxes land: bring the region's lines of I1 (read by stage 1) into L1,
-        // and at the first iteration of a level those of the coarser estimate it upsamples
+        // while the boxes land: bring the lines of I1 that stage 1 reads into L1, and at
+        // the first iteration of a level those of the coarser estimate it upsamples
         {
-            constexpr int LPR = (F::RWE * S + 127) / 128 + 1, N1 = F::RH * LPR;
+            constexpr int LPR = (F::RWE * S + 127) / 128 + 1;
             constexpr int CRH = F::RH / 2 + 2, CLPR = ((F::RWE / 2 + 2) * 8 + 127) / 128 + 1;
-            constexpr int N = N1 + (MODE == FLOW_UPSAMPLE ? CRH * CLPR : 0);
-            for (int i = threadIdx.x; i < N; i += LK_THREADS) {
-                if (i < N1)
-                    prefetch_lines_l1(a.I1, a.pitch, S, a.H, a.W, ty0 - R, ty0 - R + F::RH, tx0 - F::RE,
+            const int n1 = (F::RH - r0) * LPR;
+            const int n = n1 + (MODE == FLOW_UPSAMPLE ? CRH * CLPR : 0);
+            for (int i = threadIdx.x; i < n; i += LK_THREADS) {
+                if (i < n1)
+                    prefetch_lines_l1(a.I1, a.pitch, S, a.H, a.W, ty0 - R + r0, ty0 - R + F::RH, tx0 - F::RE,
                                       tx0 - F::RE + F::RWE, LPR, i);
                 else
-                    prefetch_lines_l1(a.fin, a.fin_pitch, 8, a.Hc, a.Wc, (ty0 - R) >> 1, ((ty0 - R) >> 1) + CRH,
-                                      (tx0 - F::RE) >> 1, ((tx0 - F::RE) >> 1) + F::RWE / 2 + 2, CLPR, i - N1);
+                    prefetch_lines_l1(a.fin, a.fin_pitch, 8, a.Hc, a.Wc, (ty0 - R) >> 1,
+                                      ((ty0 - R) >> 1) + CRH, (tx0 - F::RE) >> 1,
+                                      ((tx0 - F::RE) >> 1) + F::RWE / 2 + 2, CLPR, i - n1);
             }
         }
 #endif
@@ -1151,23 +1192,23 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
         }
         phase ^= 1u;
     }
-    // stage 1: products over the tile and its halo, by pixel pairs
+    // stage 1: products over region rows r0..RH-1 (the tile and its halo), by pixel pairs
     constexpr int NPR = F::RWE / 2;   // pairs per region row
-    constexpr int NPAIR = F::RH * NPR;
+    const int npair = (F::RH - r0) * NPR;
     const T *wt = staged ? reinterpret_cast<const T *>(win) : nullptr;
     const bool win_in_image = staged && wx0 >= 0 && wy0 >= 0 && wx0 + WW <= a.W && wy0 + F::WIN_H <= a.H;
-    // pair j = threadIdx.x + k LK_THREADS is (row ry, pair cx) of the region: stepped
-    // without a division (LK_THREADS = DY rows + DX pairs)
+    // pair j = threadIdx.x + k LK_THREADS is (row ry, pair cx) of the rows computed:
+    // stepped without a division (LK_THREADS = DY rows + DX pairs)
     constexpr int DY = LK_THREADS / NPR, DX = LK_THREADS % NPR;
-    int ry = threadIdx.x / NPR, cx = threadIdx.x % NPR;
+    int ry = r0 + threadIdx.x / NPR, cx = threadIdx.x % NPR;
 #pragma unroll 1
-    for (int j = threadIdx.x; j < NPAIR; j += LK_THREADS) {
+    for (int j = threadIdx.x; j < npair; j += LK_THREADS) {
         const int k2 = ry * (F::RWP2 / 2) + cx;   // float4 slot of the pair in the pair planes
         float4 s01, s23;
         float2 s4;
         stage1_pair<T, NC, MODE, WW>(a, tx0 - F::RE + 2 * cx, ty0 - R + ry, ref,
-                                     (SAME && staged) ? reinterpret_cast<const float4 *>(P01) + k2 : nullptr, wt,
-                                     win_in_image, wx0, wy0, F::WIN_H, s01, s23, s4);
+                                     ry < brow_end ? reinterpret_cast<const float4 *>(P01) + k2 : nullptr,
+                                     wt, win_in_image, wx0, wy0, F::WIN_H, s01, s23, s4);
         reinterpret_cast<float4 *>(P01)[k2] = s01;
         reinterpret_cast<float4 *>(P23)[k2] = s23;
         reinterpret_cast<float2 *>(P4)[ry * (F::RWP1 / 2) + cx] = s4;
@@ -1179,9 +1220,9 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
         }
     }
     __syncthreads();
-    box_h_pairs<R, TH>(P01);
-    box_h_pairs<R, TH>(P23);
-    box_h_single<R, TH>(P4);
+    box_h_pairs<R, TH>(P01, r0);
+    box_h_pairs<R, TH>(P23, r0);
+    box_h_single<R, TH>(P4, r0);
     __syncthreads();
     // vertical sums, solve and write, 4 rows of one column per item
     constexpr int VITEMS = LK_TW * (TH / 4);
@@ -1199,7 +1240,8 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
             if (y >= a.H) break;
             const float sj[5] = {s01[j].x, s01[j].y, s23[j].x, s23[j].y, s4[j]};
             float xu, xv;
-            const float2 f = solve2(sj, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv) : flow_mode<NC, MODE>(a, x, y);
+            const float2 f = solve2(sj, fp64_cond, xu, xv) ? make_float2(ref.x + xu, ref.y + xv)
+                                                           : flow_mode<NC, MODE>(a, x, y);
             if (a.fout) {
                 a.fout[(size_t)y * a.fout_pitch + x] = f;
             } else {
@@ -1209,6 +1251,40 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
         }
     }
     return true;
+}
+
+// One work unit of the fixed-radius iteration: the a.strip (1, 2 or 4) vertically
+// consecutive 64 x TH tiles of one column of tiles starting at tile row a.strip * (unit /
+// tiles_x), inside one group of REF_GROUP tile rows. All tiles of a group take the same
+// reference flow (the estimate at the group's centre column and row), so the products of
+// a region row do not depend on which tile computes them: the tiles after the first take
+// over the last 2R rows of window sums along x from the tile above instead of computing
+// their stage 1 and horizontal pass again, and the fields are the same bit for bit for
+// every a.strip. MULTI = false: a kernel whose units are single tiles (a.strip 1). Returns
+// false if a staging copy did not complete in time (then OF_ETIMEOUT is in *a.status,
+// nothing more of the unit was written, and the block must stop).
+template <typename T, bool NC, int R, int MODE, int TH = LK_TH, bool MULTI = true>
+__device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps *maps, int unit, float fp64_cond,
+                                              float *smem, uint32_t &phase)
+{
+    using F = FixedTile<R, TH>;
+    static_assert(REF_GROUP % 4 == 0, "strips of 1, 2 or 4 tiles inside a group");
+    static_assert(TH >= 2 * R && TH % 2 == 0, "the rows taken over lie below the tile above's own 2R first rows");
+    const int K = strip_len(a.strip);
+    const int uy = unit / a.tiles_x;
+    const int tx0 = (unit - uy * a.tiles_x) * LK_TW;
+    const int t_first = uy * K, t_end = min(t_first + K, (a.H + TH - 1) / TH);
+    const int gy0 = t_first / REF_GROUP * REF_GROUP * TH;
+    const float2 ref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(gy0 + REF_GROUP * TH / 2, a.H - 1));
+    if constexpr (!MULTI) {   // one tile per unit (a.strip 1)
+        return lk_tile_step<T, NC, R, MODE, TH, 0>(a, maps, tx0, t_first * TH, ref, fp64_cond, smem, phase, false);
+    } else {
+#pragma unroll 1
+        for (int t = t_first; t < t_end; ++t)
+            if (!lk_tile_step<T, NC, R, MODE, TH, 2>(a, maps, tx0, t * TH, ref, fp64_cond, smem, phase, t > t_first))
+                return false;
+        return true;
+    }
 }
 
 // ------------------------------------------------ two iterations fused in one tile
@@ -1363,7 +1439,7 @@ __device__ __forceinline__ void lk_tile_fused2(const IterArgs &a, int tile, floa
 // mode when it is known at compile time (-1: read a.mode at run time). maps: the staging
 // tensor maps in parameter space (NULL: gather from global memory). Returns false when
 // the block must stop (a staging copy timed out; recorded in *a.status).
-template <typename T, bool NC, int R, int MODE = -1, int TH = LK_TH>
+template <typename T, bool NC, int R, int MODE = -1, int TH = LK_TH, bool MULTI = true>
 __device__ __forceinline__ bool lk_tile(const IterArgs &a, const StageMaps *maps, int tile, int r, float fp64_cond,
                                         float *smem, uint32_t &phase)
 {
@@ -1371,7 +1447,7 @@ __device__ __forceinline__ bool lk_tile(const IterArgs &a, const StageMaps *maps
         lk_tile_generic<T, NC>(a, tile, r, fp64_cond, smem);
         return true;
     } else {
-        return lk_tile_fixed<T, NC, R, MODE, TH>(a, maps, tile, fp64_cond, smem, phase);
+        return lk_tile_fixed<T, NC, R, MODE, TH, MULTI>(a, maps, tile, fp64_cond, smem, phase);
     }
 }
 

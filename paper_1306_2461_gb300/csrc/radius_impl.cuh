@@ -21,7 +21,7 @@ lk_iter_kernel(const __grid_constant__ IterArgs a, const __grid_constant__ Stage
     float *smem = reinterpret_cast<float *>(smem4);
     uint32_t phase = 0;
     lk_tile_prepare<R>(smem);
-    lk_tile<T, true, R>(a, &m, blockIdx.x, r, fp64_cond, smem, phase);
+    lk_tile<T, true, R, -1, LK_TH, false>(a, &m, blockIdx.x, r, fp64_cond, smem, phase);   // a.strip is 1
 }
 
 // One iteration of up to PHASE_PAIRS pairs on one level: block b runs tile
@@ -321,7 +321,7 @@ template <int R, int TH> static bool stage_maps_th(const IterArgs &a, StageMaps 
     using F = FixedTile<R, TH>;
     const int S = elem_bytes(elem);
     if (a.mode == FLOW_SAME &&
-        !encode_tile_map(&m.flow, ET_FLOW2, a.fin, a.W, a.H, (size_t)a.fin_pitch * 8, F::RWP2, F::RH))
+        !encode_tile_map(&m.flow, ET_FLOW2, a.fin, a.W, a.H, (size_t)a.fin_pitch * 8, F::RWP2, F::FLOW_BH))
         return false;
     return encode_tile_map(&m.i2, elem, a.I2, a.W, a.H, (size_t)a.pitch * S, F::win_w(S), F::WIN_H);
 }

@@ -43,7 +43,9 @@ bool valid(const Tuning &t)
            !(t.phased && t.blocks_per_sm) && t.prefetch >= 0 && t.prefetch <= 16 &&
            (t.tile_h == 0 || t.tile_h == LK_TH || (t.tile_h == ALT_TH && t.phased && !t.generic_sums)) &&
            t.branches >= 0 && t.branches <= 4 && (t.branches <= 1 || t.phased) && t.fusion >= 0 && t.fusion <= 2 &&
-           (t.fusion <= 1 || (t.phased && !t.generic_sums && (t.tile_h == 0 || t.tile_h == LK_TH)));
+           (t.fusion <= 1 || (t.phased && !t.generic_sums && (t.tile_h == 0 || t.tile_h == LK_TH))) &&
+           (t.strip == 0 || t.strip == 1 || t.strip == 2 || t.strip == 4) &&
+           (t.strip <= 1 || (t.phased && !t.generic_sums));
 }
 
 void to_c(const Tuning &t, float ms, of_tuning *o)
@@ -56,6 +58,7 @@ void to_c(const Tuning &t, float ms, of_tuning *o)
     o->tile_h = t.tile_h ? t.tile_h : LK_TH;
     o->branches = t.branches ? t.branches : 1;
     o->fusion = t.fusion ? t.fusion : 1;
+    o->strip = tuning_strip(t);
     o->ms = ms;
 }
 
@@ -117,6 +120,7 @@ int of_tuning_set(const of_plan *method, int32_t size_class, const of_tuning *t)
     v.tile_h = t->tile_h == LK_TH ? 0 : t->tile_h;
     v.branches = t->branches == 1 ? 0 : t->branches;
     v.fusion = t->fusion == 1 ? 0 : t->fusion;
+    v.strip = t->strip == 4 ? 0 : t->strip;
     if (!valid(v)) return OF_EINVAL;
     if (v.fusion == 2 && !radius_specialised(method->radius)) return OF_EINVAL;   // fixed-radius kernels only
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -145,8 +149,9 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
     // has a specialised kernel, the per-output sums of the run-time-radius kernel; each
     // as phase launches with no L2 prefetch or one 1 or 3 blocks per SM ahead (the grouped
     // sums also with the other tile height; without prefetch also as two concurrent
-    // launch sequences over halves of the batch), and as the persistent launch at full
-    // occupancy and at 2 and 1 blocks per SM
+    // launch sequences over halves of the batch; the grouped sums in strips of 4 tiles per
+    // block, staged at the default tile height also one tile per block), and as the
+    // persistent launch at full occupancy and at 2 and 1 blocks per SM
     std::vector<Tuning> cand;
     const int occ[6] = {-1, -2, -3, 0, 2, 1};   // < 0: phase launches with prefetch pf_of[-1 - b]
     const int pf_of[3] = {0, 1, 3};
@@ -165,10 +170,21 @@ int of_autotune_batch(int32_t n, const of_handle *hs, const void *const *I1s, co
                     t.blocks_per_sm = b < 0 ? 0 : b;
                     t.prefetch = b < 0 ? pf_of[-1 - b] : 0;
                     t.tile_h = th ? ALT_TH : 0;
+                    t.strip = (t.phased && !gs) ? 0 : 1;
                     cand.push_back(t);
                     if (t.phased && t.prefetch == 0 && n > 1) {
                         t.branches = 2;
                         cand.push_back(t);
+                    }
+                    if (t.phased && !gs && sg && !th && t.prefetch == 0) {
+                        // one tile per block (every tile its own stage 1 and horizontal pass)
+                        t.strip = 1;
+                        t.branches = 0;
+                        cand.push_back(t);
+                        if (n > 1) {
+                            t.branches = 2;
+                            cand.push_back(t);
+                        }
                     }
                 }
     // iteration fusion depth 2 (grouped sums, default tile height, phase launches), in one

@@ -59,7 +59,8 @@ class Tuning(ctypes.Structure):
     """of_tuning: how a batched launch runs (see include/of.h)."""
     _fields_ = [("generic_sums", ctypes.c_int32), ("stage_i2", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("phased", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("branches", ctypes.c_int32), ("fusion", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("branches", ctypes.c_int32), ("fusion", ctypes.c_int32), ("strip", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -319,10 +320,10 @@ def tuning_get(method: Plan, size_class: int) -> dict | None:
 
 
 def tuning_set(method: Plan, size_class: int, generic_sums=0, stage_i2=1, blocks_per_sm=0, phased=1, prefetch=0,
-               tile_h=0, branches=0, fusion=1):
+               tile_h=0, branches=0, fusion=1, strip=4):
     """of_tuning_set; the defaults are the library's tuning without a table entry."""
     t = Tuning(int(generic_sums), int(stage_i2), int(blocks_per_sm), int(phased), int(prefetch), int(tile_h),
-               int(branches), int(fusion), 0.0)
+               int(branches), int(fusion), int(strip), 0.0)
     _check(_lib.of_tuning_set(ctypes.byref(method), int(size_class), ctypes.byref(t)), "of_tuning_set")
 
 

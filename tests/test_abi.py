@@ -127,6 +127,16 @@ def test_tuning_table_host_calls(of):
         of.tuning_set(m, 20, fusion=2, phased=0)                          # of the phase launches
     with pytest.raises(of.OfError):
         of.tuning_set(of.Plan.make(64, 64, 3, 7, 3, bits=12), 20, fusion=2)   # a fixed-radius kernel
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, strip=3)                                     # strips of 1, 2 or 4 tiles
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, strip=2, generic_sums=1, stage_i2=0)         # of the grouped sums
+    with pytest.raises(of.OfError):
+        of.tuning_set(m, 20, strip=2, phased=0)                           # of the phase launches
+    of.tuning_set(m, 20, strip=1)
+    assert of.tuning_get(m, 20)["strip"] == 1
+    of.tuning_set(m, 20, strip=0)                                         # 0: the default
+    assert of.tuning_get(m, 20)["strip"] == 4
     of.tuning_set(m, 20, fusion=2)
     assert of.tuning_get(m, 20)["fusion"] == 2
     of.tuning_set(m, 20, branches=3)

@@ -43,11 +43,13 @@ def test_every_candidate_matches_the_per_pair_path(of, oracle_mod):
     torch.cuda.synchronize()
     best, cands = of.autotune_batch(flows, I1, I2, reps=2)
     print(best, cands)
-    assert len(cands) == 28 and best["ms"] == min(c["ms"] for c in cands)
-    assert sum(c["branches"] == 2 for c in cands) == 6 and sum(c["fusion"] == 2 for c in cands) == 2
+    assert len(cands) == 30 and best["ms"] == min(c["ms"] for c in cands)
+    assert sum(c["branches"] == 2 for c in cands) == 7 and sum(c["fusion"] == 2 for c in cands) == 2
+    assert sum(c["strip"] == 1 and c["phased"] == 1 and c["generic_sums"] == 0 for c in cands) == 2
     sc = of.batch_size_class(flows)
     t = of.tuning_get(flows[0].plan, sc)
-    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches", "fusion")
+    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches", "fusion",
+            "strip")
     assert tuple(t[k] for k in keys) == tuple(best[k] for k in keys)
     for c in cands:
         of.tuning_set(flows[0].plan, sc, *(c[k] for k in keys))
@@ -76,12 +78,13 @@ def test_cache_file_round_trip(of, tmp_path):
     path = str(tmp_path / "tune.json")
     ent = autotune.tune(flows, I1, I2, reps=1, path=path)
     sc = of.batch_size_class(flows)
-    assert ent["size_class"] == sc and len(ent["candidates"]) == 28
+    assert ent["size_class"] == sc and len(ent["candidates"]) == 30
     of.tuning_clear()
     assert of.tuning_get(flows[0].plan, sc) is None
     assert autotune.load(path) == 1
     t = of.tuning_get(flows[0].plan, sc)
-    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches", "fusion")
+    keys = ("generic_sums", "stage_i2", "blocks_per_sm", "phased", "prefetch", "tile_h", "branches", "fusion",
+            "strip")
     assert tuple(t[k] for k in keys) == tuple(ent["best"][k] for k in keys)
     again = autotune.ensure(flows, I1, I2, path=path)      # known: no new timing
     assert again["candidates"] == [] and again["best"]["generic_sums"] == ent["best"]["generic_sums"]
@@ -125,6 +128,48 @@ def test_tall_tile_every_radius_ragged(of, oracle_mod, r):
     of.tuning_clear()
     for f in flows:
         f.close()
+
+
+@pytest.mark.parametrize("r", [2, 3, 4, 5, 6, 8, 10])
+def test_strips_equal_single_tiles_every_radius(of, r):
+    """Strips of 2 and 4 tiles per block (each tile after the first taking over the
+    window sums along x of the 2r rows it shares with the tile above) give the per-pair
+    fields (one tile per block) bit for bit, staged and gathered, FP32 and FP16 storage,
+    for every radius with a fixed-radius kernel, on sizes with partial tiles, partial
+    strips and partial reference groups (heights of 20, 97, 200 and 600 rows: 1, 5, 9 and
+    25 tile rows); at the taller tile, strips of 4 equal single tiles of that height."""
+    import torch
+    sizes = [(97, 130), (200, 333), (20, 200), (600, 72)]
+    pairs = [synth.make_c1(H, W, seed=80 + k) for k, (H, W) in enumerate(sizes)]
+    for storage in ("f32", "f16"):
+        flows = [of.Flow(of.Plan.make(H, W, 3, r, 4, bits=8, storage=storage)) for H, W in sizes]
+        I1 = [to_dev(p.I1) for p in pairs]
+        I2 = [to_dev(p.I2) for p in pairs]
+        ref = []
+        for k, (H, W) in enumerate(sizes):
+            with of.Flow(of.Plan.make(H, W, 3, r, 4, bits=8, storage=storage)) as f:
+                u, v = f.compute(I1[k], I2[k])
+                ref.append((u.clone(), v.clone()))
+        sc = of.batch_size_class(flows)
+        for stage in (1, 0):
+            for strip in (1, 2, 4):
+                of.tuning_set(flows[0].plan, sc, stage_i2=stage, strip=strip)
+                assert of.tuning_get(flows[0].plan, sc)["strip"] == strip
+                us, vs = of.compute_batch(flows, I1, I2)
+                torch.cuda.synchronize()
+                for k in range(len(sizes)):
+                    assert torch.equal(us[k], ref[k][0]) and torch.equal(vs[k], ref[k][1]), (storage, stage, strip, k)
+        tall = {}
+        for strip in (1, 4):
+            of.tuning_set(flows[0].plan, sc, tile_h=32, strip=strip)
+            us, vs = of.compute_batch(flows, I1, I2)
+            torch.cuda.synchronize()
+            tall[strip] = [(u.clone(), v.clone()) for u, v in zip(us, vs)]
+        for k in range(len(sizes)):
+            assert torch.equal(tall[1][k][0], tall[4][k][0]) and torch.equal(tall[1][k][1], tall[4][k][1]), (storage, k)
+        of.tuning_clear()
+        for f in flows:
+            f.close()
 
 
 @pytest.mark.parametrize("r", [2, 3, 4, 5, 6, 8, 10])
