@@ -209,10 +209,11 @@ int of_compute_batch_host(int32_t n, const of_handle *hs, const void *const *hI1
  *                  tolerance, the reference flows of the region's pixels being the tile's);
  *                  0 or 1: one iteration per launch
  *   strip          phase launches with grouped sums: tiles per block along a column of
- *                  tiles, 1, 2 or 4 (0 means 4). The tiles of a group of 4 tile rows share
- *                  one reference flow, so a block's tiles after the first take over the
- *                  window sums of the rows they share with the tile above; the fields are
- *                  the same bit for bit for every strip (of_compute runs strip 1)
+ *                  tiles, 1, 2 or 4 (0 means 4), halved for a launch while it would have
+ *                  fewer than 8 blocks per SM. The tiles of a group of 4 tile rows share one
+ *                  reference flow, so a block's tiles after the first take over the window
+ *                  sums of the rows they share with the tile above; the fields are the
+ *                  same bit for bit for every strip (of_compute runs strip 1)
  *   ms             measured milliseconds per batch (of_autotune_batch output only)
  * The process-wide table is keyed by the method (in_format, storage, radius, levels,
  * iterations, OF_FLAG_ZNSSD, OF_FLAG_I1GRAD) and a size class, round(log2(mean level-0 pixels

@@ -14,6 +14,12 @@
 
 #include "batch_device.cuh"
 
+// Strips of the phase launches shrink while a launch would have fewer blocks than this
+// many per resident block slot.
+#ifndef OF_STRIP_WAVES
+#define OF_STRIP_WAVES 2
+#endif
+
 namespace of {
 
 // The bounded-wait test kernel (of_debug_wait_timeout) runs the barrier's wait loop on
@@ -342,6 +348,15 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
             memset(&I, 0, sizeof(I));
             I.npairs = m;
             I.ahead = prefetch_ahead;
+            // strips as long as the tuning's while the launch keeps OF_STRIP_WAVES blocks per
+            // resident block slot (4 per SM) or more; the fields do not depend on the strip length
+            int kl = strip;
+            if (kl > 1) {
+                long tiles_l = 0;
+                for (int i = 0; i < m; ++i)
+                    tiles_l += strip_units(bp[i].H[l], bp[i].W[l], tile_h, 1);
+                while (kl > 1 && tiles_l < (long)kl * OF_STRIP_WAVES * 4 * sms) kl /= 2;
+            }
             for (int i = 0; i < m; ++i) {
                 IterArgs &a = I.a[i];
                 a.I1 = bp[i].pyr[0] + bp[i].off[l];
@@ -371,7 +386,7 @@ static cudaError_t enqueue_chain(const BatchPair *pairs, int n, const of_plan &p
                 a.tiles_x = (a.W + LK_TW - 1) / LK_TW;
                 // the variant's kernels and the fused kernel have their own tile height
                 const int th = i1grad ? I1_TH : (two ? LK_TH : tile_h);
-                a.strip = (i1grad || two) ? 1 : strip;
+                a.strip = (i1grad || two) ? 1 : kl;
                 a.tiles = strip_units(a.H, a.W, th, a.strip);
                 a.status = bp[i].status;
                 a.stage_i2 = (i1grad || two) ? 0 : stage;   // the fused kernel gathers
