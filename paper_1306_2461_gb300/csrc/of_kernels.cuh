@@ -986,29 +986,61 @@ __device__ __forceinline__ void box_h_single(float *P, int r0 = 0)
     }
 }
 
-// Vertical pass for the 4 outputs (rows 4g..4g+3, column tx): sums of the three planes.
+// o[j] = sum_{k=0}^{2R} v[j+k], j = 0..5, from v[0 .. 2R+5] (R >= 3): the rows 5..2R that
+// all six windows share summed once, the others as partial sums from either end.
+template <int R, typename V>
+__device__ __forceinline__ void box6v(const V *v, V o[6])
+{
+    static_assert(R >= 3, "six windows with a shared middle");
+    V m = v[5];
+#pragma unroll
+    for (int k = 6; k <= 2 * R; ++k) m = vadd(m, v[k]);
+    V lf[5], rt[6];
+    lf[4] = v[4];
+#pragma unroll
+    for (int j = 3; j >= 0; --j) lf[j] = vadd(v[j], lf[j + 1]);
+    rt[1] = v[2 * R + 1];
+#pragma unroll
+    for (int j = 2; j <= 5; ++j) rt[j] = vadd(rt[j - 1], v[2 * R + j]);
+    o[0] = vadd(lf[0], m);
+#pragma unroll
+    for (int j = 1; j <= 4; ++j) o[j] = vadd(vadd(lf[j], m), rt[j]);
+    o[5] = vadd(m, rt[5]);
+}
+
+// Output rows per item of the vertical pass: 6 where they tile the tile height (for TH =
+// 24 one item per thread of a 256-thread block), else 4.
+template <int R, int TH> constexpr int v_rows() { return (TH % 6 == 0 && R >= 3) ? 6 : 4; }
+
+// Vertical pass for the VR = v_rows outputs of item g (rows VR g .. VR g + VR - 1, column
+// tx): sums of the three planes.
 template <int R, int TH, int TW = LK_TW>
 __device__ __forceinline__ void box_v_planes(const float2 *P01, const float2 *P23, const float *P4, int g, int tx,
-                                             float2 s01[4], float2 s23[4], float s4[4])
+                                             float2 s01[v_rows<R, TH>()], float2 s23[v_rows<R, TH>()],
+                                             float s4[v_rows<R, TH>()])
 {
     using F = FixedTile<R, TH, TW>;
+    constexpr int VR = v_rows<R, TH>(), NV = 2 * R + VR;
     {
-        float2 v[2 * R + 4];
+        float2 v[NV];
 #pragma unroll
-        for (int q = 0; q < 2 * R + 4; ++q) v[q] = P01[(4 * g + q) * F::RWP2 + tx];
-        box4v<R, 0>(v, s01);
+        for (int q = 0; q < NV; ++q) v[q] = P01[(VR * g + q) * F::RWP2 + tx];
+        if constexpr (VR == 6) box6v<R>(v, s01);
+        else box4v<R, 0>(v, s01);
     }
     {
-        float2 v[2 * R + 4];
+        float2 v[NV];
 #pragma unroll
-        for (int q = 0; q < 2 * R + 4; ++q) v[q] = P23[(4 * g + q) * F::RWP2 + tx];
-        box4v<R, 0>(v, s23);
+        for (int q = 0; q < NV; ++q) v[q] = P23[(VR * g + q) * F::RWP2 + tx];
+        if constexpr (VR == 6) box6v<R>(v, s23);
+        else box4v<R, 0>(v, s23);
     }
     {
-        float v[2 * R + 4];
+        float v[NV];
 #pragma unroll
-        for (int q = 0; q < 2 * R + 4; ++q) v[q] = P4[(4 * g + q) * F::RWP1 + tx];
-        box4v<R, 0>(v, s4);
+        for (int q = 0; q < NV; ++q) v[q] = P4[(VR * g + q) * F::RWP1 + tx];
+        if constexpr (VR == 6) box6v<R>(v, s4);
+        else box4v<R, 0>(v, s4);
     }
 }
 
@@ -1224,19 +1256,20 @@ __device__ __forceinline__ bool lk_tile_step(const IterArgs &a, const StageMaps 
     box_h_pairs<R, TH>(P23, r0);
     box_h_single<R, TH>(P4, r0);
     __syncthreads();
-    // vertical sums, solve and write, 4 rows of one column per item
-    constexpr int VITEMS = LK_TW * (TH / 4);
+    // vertical sums, solve and write, VR rows of one column per item
+    constexpr int VR = v_rows<R, TH>();
+    constexpr int VITEMS = LK_TW * (TH / VR);
 #pragma unroll 1
     for (int i = threadIdx.x; i < VITEMS; i += LK_THREADS) {
         const int tx = i % LK_TW, g = i / LK_TW;
         const int x = tx0 + tx;
-        if (x >= a.W || ty0 + 4 * g >= a.H) continue;
-        float2 s01[4], s23[4];
-        float s4[4];
+        if (x >= a.W || ty0 + VR * g >= a.H) continue;
+        float2 s01[VR], s23[VR];
+        float s4[VR];
         box_v_planes<R, TH>(P01, P23, P4, g, tx, s01, s23, s4);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int y = ty0 + 4 * g + j;
+        for (int j = 0; j < VR; ++j) {
+            const int y = ty0 + VR * g + j;
             if (y >= a.H) break;
             const float sj[5] = {s01[j].x, s01[j].y, s23[j].x, s23[j].y, s4[j]};
             float xu, xv;
@@ -1352,17 +1385,18 @@ __device__ __forceinline__ void lk_tile_fused2(const IterArgs &a, int tile, floa
         box_h_pairs<R, X::THA, X::TWA>(Q23);
         box_h_single<R, X::THA, X::TWA>(Q4);
         __syncthreads();
-        constexpr int VITEMS = X::TWA * (X::THA / 4);
+        constexpr int VRA = v_rows<R, X::THA>();
+        constexpr int VITEMS = X::TWA * (X::THA / VRA);
 #pragma unroll 1
         for (int i = threadIdx.x; i < VITEMS; i += LK_THREADS) {
             const int tx = i % X::TWA, g = i / X::TWA;
             const int x = ax0 + tx;
-            float2 s01[4], s23[4];
-            float s4[4];
+            float2 s01[VRA], s23[VRA];
+            float s4[VRA];
             box_v_planes<R, X::THA, X::TWA>(Q01, Q23, Q4, g, tx, s01, s23, s4);
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int ryb = 4 * g + jj, y = ay0 + ryb;
+            for (int jj = 0; jj < VRA; ++jj) {
+                const int ryb = VRA * g + jj, y = ay0 + ryb;
                 if (ryb >= B::RH) break;
                 float2 f = f2(0.0f, 0.0f);   // outside the image: never read by step B
                 if ((unsigned)x < (unsigned)a.W && (unsigned)y < (unsigned)a.H) {
@@ -1407,18 +1441,19 @@ __device__ __forceinline__ void lk_tile_fused2(const IterArgs &a, int tile, floa
         box_h_pairs<R, TH>(P23);
         box_h_single<R, TH>(P4);
         __syncthreads();
-        constexpr int VITEMS = LK_TW * (TH / 4);
+        constexpr int VR = v_rows<R, TH>();
+        constexpr int VITEMS = LK_TW * (TH / VR);
 #pragma unroll 1
         for (int i = threadIdx.x; i < VITEMS; i += LK_THREADS) {
             const int tx = i % LK_TW, g = i / LK_TW;
             const int x = tx0 + tx;
-            if (x >= a.W || ty0 + 4 * g >= a.H) continue;
-            float2 s01[4], s23[4];
-            float s4[4];
+            if (x >= a.W || ty0 + VR * g >= a.H) continue;
+            float2 s01[VR], s23[VR];
+            float s4[VR];
             box_v_planes<R, TH>(P01, P23, P4, g, tx, s01, s23, s4);
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int y = ty0 + 4 * g + jj;
+            for (int jj = 0; jj < VR; ++jj) {
+                const int y = ty0 + VR * g + jj;
                 if (y >= a.H) break;
                 const float sj[5] = {s01[jj].x, s01[jj].y, s23[jj].x, s23[jj].y, s4[jj]};
                 float xu, xv;

@@ -120,15 +120,16 @@ window_sums_kernel(const float *ch, int H, int W, int r, int tiles_x, float *out
         box_h_pairs<R, LK_TH>(P23);
         box_h_single<R, LK_TH>(P4);
         __syncthreads();
-        for (int i = threadIdx.x; i < LK_TW * (LK_TH / 4); i += blockDim.x) {
+        constexpr int VR = v_rows<R, LK_TH>();
+        for (int i = threadIdx.x; i < LK_TW * (LK_TH / VR); i += blockDim.x) {
             const int tx = i % LK_TW, g = i / LK_TW;
             const int x = tx0 + tx;
             if (x >= W) continue;
-            float2 s01[4], s23[4];
-            float s4[4];
+            float2 s01[VR], s23[VR];
+            float s4[VR];
             box_v_planes<R, LK_TH>(P01, P23, P4, g, tx, s01, s23, s4);
-            for (int j = 0; j < 4; ++j) {
-                const int y = ty0 + 4 * g + j;
+            for (int j = 0; j < VR; ++j) {
+                const int y = ty0 + VR * g + j;
                 if (y >= H) break;
                 const float s[5] = {s01[j].x, s01[j].y, s23[j].x, s23[j].y, s4[j]};
                 for (int c = 0; c < 5; ++c) out[c * N + (size_t)y * W + x] = s[c];
