@@ -882,12 +882,13 @@ __device__ __forceinline__ void box4v(const V *v, V o[4])
 }
 
 // Horizontal pass of one pair plane, in place, over rows r0..RH-1: row ry becomes, at
-// columns 0..TW-1, the window sums of its outputs (two channels per float2). For 64-wide tiles a warp takes
+// columns 0..TW-1, the window sums of its outputs (two channels per float2). Chunk c of
+// rows goes to warp (c + woff) mod WARPS. For 64-wide tiles a warp takes
 // two rows and a quarter warp 4 groups of 4 outputs of each (with rows RWP2 = 2 mod 4
 // float2 long, its 16-byte reads hit distinct banks); other widths take one row per warp,
 // one group per lane. Each row is read and rewritten by one warp.
 template <int R, int TH, int TW = LK_TW>
-__device__ __forceinline__ void box_h_pairs(float2 *P, int r0 = 0)
+__device__ __forceinline__ void box_h_pairs(float2 *P, int r0 = 0, int woff = 0)
 {
     using F = FixedTile<R, TH, TW>;
     static_assert(LK_THREADS % 32 == 0, "whole warps");
@@ -899,7 +900,7 @@ __device__ __forceinline__ void box_h_pairs(float2 *P, int r0 = 0)
     const int rsub = TWO ? (lane >> 2) & 1 : 0, g = TWO ? (((lane >> 3) << 2) | (lane & 3)) : lane;
     const int rows = TWO ? (F::RH - r0) / 2 : F::RH - r0;   // warp-sized chunks (r0, RH - r0 even)
 #pragma unroll 1
-    for (int chunk = threadIdx.x >> 5; chunk < rows; chunk += WARPS) {
+    for (int chunk = ((threadIdx.x >> 5) + WARPS - woff) % WARPS; chunk < rows; chunk += WARPS) {
         const bool act = TWO || g < NG;
         float4 *row = reinterpret_cast<float4 *>(P) + ((r0 + (TWO ? 2 * chunk + rsub : chunk)) * RW4 + 2 * g);
         float2 o[4];
@@ -1252,8 +1253,10 @@ __device__ __forceinline__ bool lk_tile_step(const IterArgs &a, const StageMaps 
         }
     }
     __syncthreads();
+    // P23's chunks start at warp 4, so that when the rows leave some warps an extra chunk
+    // of P01 and of P4 (24 rows: 12 chunks and 384 items) the other warps take P23's
     box_h_pairs<R, TH>(P01, r0);
-    box_h_pairs<R, TH>(P23, r0);
+    box_h_pairs<R, TH>(P23, r0, LK_THREADS / 64);
     box_h_single<R, TH>(P4, r0);
     __syncthreads();
     // vertical sums, solve and write, VR rows of one column per item
