@@ -63,6 +63,16 @@ def algorithmic_bytes(H, W, L, n, s, raw):
     return pyr + it, pyr, it
 
 
+def unfused_dataflow_bytes(H, W, L, n, s, raw):
+    """The same count for the plain dataflow without this implementation's two savings:
+    the first reduction re-reads level 0 instead of taking it from the raw read, and every
+    iteration reads a full-level estimate (none is skipped at the very first, none comes
+    from the coarser level): pyramids read raw, write every level and read levels
+    0..L-2 once; iterations read I1, I2 (s each) and the estimate (8 B) and write (8 B)."""
+    N = [h * w for h, w in level_sizes(H, W, L)]
+    return 2 * (raw * N[0] + s * sum(N) + s * sum(N[:L - 1])) + n * sum(N) * (2 * s + 16)
+
+
 def algorithmic_bytes_i1grad(H, W, L, n, s, raw):
     """The same for the first-image-gradient variant: per level the window matrices are
     written once (16 B/px, after reading I1 at s B/px) and read by every iteration."""
@@ -449,6 +459,11 @@ def main():
                      "timed_unit": "one step = one CUDA graph launch, CUDA events around each on the launching stream",
                      "algorithmic_bytes_per_step": alg * B,
                      "algorithmic_bytes_per_field": {"total": alg, "pyramids": alg_pyr, "iterations": alg_it},
+                     "unfused_dataflow": None if args.i1grad else {
+                         "bytes_per_field": unfused_dataflow_bytes(H, W, LEVELS, ITERS, 2, 2),
+                         "frac": unfused_dataflow_bytes(H, W, LEVELS, ITERS, 2, 2) * B / (launch_ms / 1000.0) / 1e9 / peak,
+                         "note": "the same time against the byte count of a dataflow that re-reads level 0 for the "
+                                 "first reduction and reads a full-level estimate at every iteration"},
                      "kernel_source_sha1": khash},
         "gpu_launches": args.steps * launches_per_step,
         "host_wall_s": t_host,
