@@ -95,13 +95,14 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
             return OF_EINVAL;
         if (!hI1s[i] && !hs[i]->has_prev) return OF_ESTATE;
     }
-    // default: chunks of about three 1024^2 pairs (measured on 64 such pairs: 3 pairs per
-    // chunk beat 4, 6, 8 and 11), at most 24 chunks
+    // default: chunks of about eight 1024^2 pairs, at most 24 chunks (measured on 64 such
+    // pairs, fields/s for 3, 4, 6, 8, 11, 16, 22, 32 pairs per chunk: 9343, 9434, 9517, 9656,
+    // 9430, 9146, 8782, 7915; from 8 pairs on, a chunk's launches have the tiles for strips)
     int per = chunk;
     if (per <= 0) {
         double px = 0.0;
         for (int i = 0; i < n; ++i) px += (double)hs[i]->plan.H * hs[i]->plan.W;
-        per = (int)lround(3.0 * 1048576.0 / (px / n));
+        per = (int)lround(8.0 * 1048576.0 / (px / n));
         per = std::max(per, std::max(1, (n + 23) / 24));
     }
     const int nch = (n + per - 1) / per;
