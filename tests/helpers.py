@@ -15,7 +15,8 @@ Which pixels are compared (parity_check):
 Every exclusion is counted and bounded. The implementation check compares the CUDA
 path with the oracle run on the pyramid stored as the CUDA path stores it (level 0
 exact, reduced levels rounded to the storage type), so both sides see the same
-inputs. The storage check (FP16/BF16 against the unrounded FP64 oracle) applies the
+inputs and only the arithmetic differs: it applies the FP32 bound (IMPL_TOL) whatever
+the storage. The storage check (FP16/BF16 against the unrounded FP64 oracle) applies the
 stated max and RMS bounds to the compared pixels whose FP64 result moves by less than
 half the tolerance when the pyramid is rounded; the others ("storage-sensitive": the
 method itself does not determine them to the tolerance from inputs known to the
@@ -24,6 +25,7 @@ storage precision) are counted and bounded.
 import numpy as np
 
 TOL = {"f32": (1e-3, None), "f16": (2e-2, 5e-3), "bf16": (2e-1, 5e-2)}
+IMPL_TOL = TOL["f32"][0]   # FP32 arithmetic against FP64 on identical stored inputs
 
 
 def to_dev(a):
@@ -175,7 +177,7 @@ def parity_check(u, v, pair_or_imgs, oracle_mod, L, r, n, storage, label="", mar
           f"{int(unstable.sum())}); vs oracle on the same stored pyramid: max {impl['max']:.3e} rms "
           f"{impl['rms']:.3e}; vs unrounded FP64 oracle: max {st['max']:.3e} rms {st['rms']:.3e}, "
           f"storage-sensitive {int(sens.sum())}, max on the rest {sm['max']:.3e}; whole image max {full.max():.3e}")
-    assert impl["max"] <= tmax, impl
+    assert impl["max"] <= IMPL_TOL, impl
     if workload:
         if trms is not None:
             assert sm["rms"] <= trms, sm
