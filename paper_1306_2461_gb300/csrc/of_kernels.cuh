@@ -1227,29 +1227,45 @@ __device__ __forceinline__ bool lk_tile_step(const IterArgs &a, const StageMaps 
     }
     // stage 1: products over region rows r0..RH-1 (the tile and its halo), by pixel pairs
     constexpr int NPR = F::RWE / 2;   // pairs per region row
-    const int npair = (F::RH - r0) * NPR;
     const T *wt = staged ? reinterpret_cast<const T *>(win) : nullptr;
     const bool win_in_image = staged && wx0 >= 0 && wy0 >= 0 && wx0 + WW <= a.W && wy0 + F::WIN_H <= a.H;
-    // pair j = threadIdx.x + k LK_THREADS is (row ry, pair cx) of the rows computed:
-    // stepped without a division (LK_THREADS = DY rows + DX pairs)
-    constexpr int DY = LK_THREADS / NPR, DX = LK_THREADS % NPR;
-    int ry = r0 + threadIdx.x / NPR, cx = threadIdx.x % NPR;
-#pragma unroll 1
-    for (int j = threadIdx.x; j < npair; j += LK_THREADS) {
+    auto pair = [&](int ry, int cx) {
         const int k2 = ry * (F::RWP2 / 2) + cx;   // float4 slot of the pair in the pair planes
         float4 s01, s23;
         float2 s4;
         stage1_pair<T, NC, MODE, WW>(a, tx0 - F::RE + 2 * cx, ty0 - R + ry, ref,
-                                     ry < brow_end ? reinterpret_cast<const float4 *>(P01) + k2 : nullptr,
-                                     wt, win_in_image, wx0, wy0, F::WIN_H, s01, s23, s4);
+                                     ry < brow_end ? reinterpret_cast<const float4 *>(P01) + k2 : nullptr, wt,
+                                     win_in_image, wx0, wy0, F::WIN_H, s01, s23, s4);
         reinterpret_cast<float4 *>(P01)[k2] = s01;
         reinterpret_cast<float4 *>(P23)[k2] = s23;
         reinterpret_cast<float2 *>(P4)[ry * (F::RWP1 / 2) + cx] = s4;
-        ry += DY;
-        cx += DX;
-        if (cx >= NPR) {
-            cx -= NPR;
-            ++ry;
+    };
+    if constexpr (CM == 2) {
+        // strips: thread t takes pixel pair cx = t mod NPR of rows r0 + t / NPR, then RPI
+        // rows further each round, so that what depends on the pair's column is the same on
+        // every row it takes (5% fewer instructions per pixel-iteration at r = 4)
+        constexpr int RPI = LK_THREADS / NPR;   // rows per round
+        const int cx = threadIdx.x % NPR, rs = threadIdx.x / NPR;
+        if (rs < RPI) {
+#pragma unroll 1
+            for (int ry = r0 + rs; ry < F::RH; ry += RPI) pair(ry, cx);
+        }
+    } else {
+        // single tiles: pair j = threadIdx.x + k LK_THREADS is (row ry, pair cx) of the rows
+        // computed, stepped without a division (LK_THREADS = DY rows + DX pairs); it
+        // compiles without spills where the form above does not
+        constexpr int DY = LK_THREADS / NPR, DX = LK_THREADS % NPR;
+        const int npair = (F::RH - r0) * NPR;
+        int ry = r0 + threadIdx.x / NPR, cx = threadIdx.x % NPR;
+#pragma unroll 1
+        for (int j = threadIdx.x; j < npair; j += LK_THREADS) {
+            pair(ry, cx);
+            ry += DY;
+            cx += DX;
+            if (cx >= NPR) {
+                cx -= NPR;
+                ++ry;
+            }
         }
     }
     __syncthreads();
