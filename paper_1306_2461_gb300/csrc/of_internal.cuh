@@ -148,10 +148,12 @@ static_assert(sizeof(IterPhase) <= 32000 && sizeof(PyrPhase) <= 32000, "kernel p
 
 // Tile shapes.
 constexpr int LK_TW = 64;    // iteration output tile width
-// Iteration output tile: 64 x 24 at 4 blocks of 256 threads per SM (measured at the 1024^2,
-// r = 4 batch with staging: 64 x 24 at 4 blocks 6.66 ms per step, 64 x 32 at 3 blocks 6.87,
-// 64 x 20 at 4 blocks 7.11; with 512-thread blocks at 2 per SM 64 x 56 6.75, 64 x 48
-// 6.87). The height can be set at build time (a multiple of 4).
+// Iteration output tile: 64 x 24 at 4 blocks of 256 threads per SM (measured on the 1024^2,
+// r = 4 batch with staging and strips of 4 tiles: 64 x 24 5.54 ms per step, 64 x 32 at 3
+// blocks 6.01, 64 x 16 at 5 blocks (48 registers, spills) 6.95; before strips, 64 x 20 at 4
+// blocks 7.11 and, with 512-thread blocks at 2 per SM, 64 x 56 6.75 against 6.66 for 64 x 24).
+// At 24 rows the vertical pass's six-row items are one per thread. The height can be set at
+// build time (a multiple of 4).
 #ifndef OF_LK_TH
 #define OF_LK_TH 24
 #endif

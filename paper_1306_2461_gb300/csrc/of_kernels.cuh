@@ -594,7 +594,7 @@ template <int R, int TH = LK_TH, int TW = LK_TW> struct FixedTile {
     static constexpr int NREG = RH * RW;               // region pixels
     static constexpr int PER = (NREG + LK_THREADS - 1) / LK_THREADS;   // region pixels per thread
     // Staging (a.stage_i2): one TMA box of I2, the window of the tile's region shifted by
-    // the tile's rounded reference flow and widened by STAGE_MARGIN pixels plus the 4x4
+    // the rounded estimate at the tile's centre and widened by STAGE_MARGIN pixels plus the 4x4
     // tap footprint (and, for the alignment of its first column, E - 1 columns), in the
     // storage type: WIN_W(S) x WIN_H elements of S bytes, rows WIN_W(S) elements apart.
     // A pixel whose taps leave it reads them from global memory instead.

@@ -47,3 +47,21 @@ def test_pixel_iterations_per_field_of_the_workloads():
     assert bench.pixel_iterations(1024, 1024, 3, 5) == 6_881_280
     assert bench.pixel_iterations(2048, 2048, 4, 6) == 33_423_360
     assert bench.pixel_iterations(383, 1791, 3, 1) == 383 * 1791 + 192 * 896 + 96 * 448
+
+
+def test_algorithmic_bytes_of_the_headline_workload():
+    # 1024^2, 12-bit camera counts (2 B), FP16 reduced levels, L = 3, n = 5, counted by hand:
+    # levels of 1,048,576, 262,144 and 65,536 px; per pixel-iteration I1 + I2 (2 x 2 B) and
+    # the estimate in and out (8 + 8 B), except that a level's first iteration reads the
+    # coarser level's estimate (the very first none); pyramids: the raw read and level-0
+    # copy (2 + 2 B per px, both images), levels 1 and 2 written, level 1 read once.
+    sys.path.insert(0, ROOT)
+    import bench
+    N = [1048576, 262144, 65536]
+    pyr = 2 * (2 * N[0] + 2 * N[0] + 2 * (N[1] + N[2]) + 2 * N[1])
+    it = sum(5 * N[l] * (4 + 8) + 4 * N[l] * 8 for l in range(3)) + 8 * N[1] + 8 * N[2]
+    assert bench.algorithmic_bytes(1024, 1024, 3, 5, 2, 2) == (pyr + it, pyr, it) == (139984896, 10747904, 129236992)
+    # the plain dataflow: level 0 re-read for the first reduction, every iteration reading a
+    # full-level estimate
+    plain = 2 * (2 * N[0] + 2 * sum(N) + 2 * (N[0] + N[1])) + 5 * sum(N) * 20
+    assert bench.unfused_dataflow_bytes(1024, 1024, 3, 5, 2, 2) == plain == 152567808
