@@ -100,9 +100,9 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(kernel_hash, variant=False):
-    """DRAM bytes per step (all kernels of one graph replay) from the committed ncu
-    summary, if it was taken on this exact kernel source (else None)."""
+def recorded_traffic(kernel_hash, variant=False, key="bytes_per_step_full_batch"):
+    """DRAM bytes per step (all kernels of one graph replay; or another recorded `key`) from
+    the committed ncu summary, if it was taken on this exact kernel source (else None)."""
     name = "batch_step_i1grad_pair1024_traffic.txt" if variant else "batch_step_pair1024_traffic.txt"
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
@@ -115,9 +115,46 @@ def recorded_traffic(kernel_hash, variant=False):
     if kv.get("kernel_source_sha1") != kernel_hash:
         return None
     try:
-        return float(kv["bytes_per_step_full_batch"])
+        return float(kv[key])
     except (KeyError, ValueError):
         return None
+
+
+def dominant_kernel_leg(torch, of, I1, I2, stream, peak, khash, pairs=32, reps=20):
+    """The level-0 same-level iteration (the step's dominant kernel) timed live: one-level
+    plans run one zero-start iteration, then same-level ones, each a phase launch over the
+    batch; 6 and 2 iterations differ by 4 same-level launches that write the interleaved
+    estimate, as the level-0 iterations of the step do (the step's sequences are 32 pairs
+    each). CUDA events around `reps` graph replays of each on the launching stream."""
+    n = min(pairs, len(I1))
+    ms = {}
+    for iters in (2, 6):
+        plan = of.Plan.make(H, W, 1, RADIUS, iters, bits=BITS, storage="f16")
+        flows = [of.Flow(plan) for _ in range(n)]
+        us = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(n)]
+        vs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(n)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                of.compute_batch(flows, I1[:n], I2[:n], us, vs, stream=stream)
+            stream.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                of.compute_batch(flows, I1[:n], I2[:n], us, vs, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+        ms[iters] = a.elapsed_time(b) / reps
+        for f in flows:
+            f.close()
+    launch_ms = (ms[6] - ms[2]) / 4
+    alg = n * H * W * (2 * 2 + 8 + 8)
+    achieved = alg / (launch_ms / 1000.0) / 1e9
+    traffic = recorded_traffic(khash, key="dominant_kernel_bytes_per_launch") if n == 32 else None
+    return {"kernel": "phase_iter_kernel<uint16_t, 4, SAME, 24> (level-0 same-level iteration)",
+            "pairs_per_launch": n, "launch_us": launch_ms * 1000.0, "algorithmic_bytes_per_launch": alg,
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "method": "one-level batches of 6 and 2 iterations timed with CUDA events on the launching stream; "
+                      "their difference is 4 same-level launches"}
 
 
 def cpu_model():
@@ -425,6 +462,8 @@ def main():
     khash = kernel_source_hash()
     traffic = recorded_traffic(khash, args.i1grad)
     clocks = clk.summary()
+    # the dominant kernel alone, timed live (after the timed region, rank 0)
+    dominant = None if args.i1grad else dominant_kernel_leg(torch, of, I1, I2, stream, peak, khash)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -464,6 +503,7 @@ def main():
                          "frac": unfused_dataflow_bytes(H, W, LEVELS, ITERS, 2, 2) * B / (launch_ms / 1000.0) / 1e9 / peak,
                          "note": "the same time against the byte count of a dataflow that re-reads level 0 for the "
                                  "first reduction and reads a full-level estimate at every iteration"},
+                     "dominant_kernel": dominant,
                      "kernel_source_sha1": khash},
         "gpu_launches": args.steps * launches_per_step,
         "host_wall_s": t_host,
