@@ -626,7 +626,8 @@ template <int R, int TH = LK_TH, int TW = LK_TW> struct FixedTile {
     static constexpr int PLANES = 4 * PAIR_PLANE + RH * RWP1;  // floats of the three planes
     static_assert(PLANES % 4 == 0, "the barrier after the planes must be 8-byte aligned");
     static constexpr int OFF_BAR = PLANES;                    // 8-byte mbarrier
-    static constexpr int OFF_WIN = (OFF_BAR + 2 + 31) / 32 * 32;   // 128-byte aligned staging window
+    static constexpr int OFF_WREF = OFF_BAR + 2;              // a strip's tile-centre estimates (4 float2)
+    static constexpr int OFF_WIN = (OFF_WREF + 8 + 31) / 32 * 32;   // 128-byte aligned staging window
     static constexpr int SMEM_NOSTAGE = OFF_WIN;              // launches without staging
     static constexpr int smem_staged(int S) { return OFF_WIN + (win_bytes(S) + 15) / 16 * 4; }
     static constexpr int SMEM_FLOATS = smem_staged(4);        // the largest (FP32 storage)
@@ -656,6 +657,11 @@ template <int R, int TH = LK_TH, int TW = LK_TW> struct FixedTile {
 // the shared-memory carve-out leaves of L1; 2 measured 1.9% faster per batch step than 0.
 #ifndef OF_PREFETCH_I1
 #define OF_PREFETCH_I1 2
+#endif
+// Strips: request a later tile's window of I2 while the tile above finishes (1), or at
+// the tile's own staging (0).
+#ifndef OF_EARLY_WINDOW
+#define OF_EARLY_WINDOW 1
 #endif
 constexpr long long STAGE_TIMEOUT_NS = 200000000LL;   // 0.2 s for one tile's staging copies
 
@@ -1113,6 +1119,29 @@ __device__ __forceinline__ void stage1_pair(const IterArgs &a, int x, int y, flo
     }
 }
 
+// The estimate that places the staged window of the 64 x TH tile at (tx0, ty0): the one at
+// the tile's centre.
+template <bool NC, int MODE, int TH>
+__device__ __forceinline__ float2 win_ref(const IterArgs &a, int tx0, int ty0)
+{
+    return flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + TH / 2, a.H - 1));
+}
+
+// First element (wx0, wy0) of the staged window of the tile at (tx0, ty0) for the estimate
+// w at its centre: the tile's region displaced by w rounded, widened by the margin and the
+// tap footprint, wx0 rounded down to a multiple of 16 bytes.
+template <int R, int TH, int S>
+__device__ __forceinline__ void win_origin(const IterArgs &a, int tx0, int ty0, float2 w, int &wx0, int &wy0)
+{
+    using F = FixedTile<R, TH>;
+    constexpr int E = 16 / S;
+    const int ox = __float2int_rn(fminf(fmaxf(w.x, -(float)a.W), (float)a.W));
+    const int oy = __float2int_rn(fminf(fmaxf(w.y, -(float)a.H), (float)a.H));
+    const int wx = tx0 - F::RE + ox - F::STAGE_MARGIN - 2;
+    wx0 = (wx >= 0 ? wx / E : -((-wx + E - 1) / E)) * E;
+    wy0 = ty0 - R + oy - F::STAGE_MARGIN - 2;
+}
+
 // The tile's mbarrier: initialised once per block, before the first tile.
 template <int R, int TH = LK_TH> __device__ __forceinline__ void lk_tile_init(float *smem)
 {
@@ -1125,11 +1154,15 @@ template <int R, int TH = LK_TH> __device__ __forceinline__ void lk_tile_init(fl
 
 // One tile of a work unit (lk_tile_fixed). A tile after the first of its strip takes over
 // region rows 0..2R-1 from the tile above; CM = 0: a first tile, 1: a later one, 2: as
-// `carry_rt` says at run time (one body for both, the loop of a strip). Returns false if
-// a staging copy did not complete in time.
+// `carry_rt` says at run time (one body for both, the loop of a strip). At CM 2 with
+// staging, wrefs[0] is this tile's window estimate (win_ref) and wrefs[1] the next one's
+// when `next` (a tile of the same strip follows): that tile's window is then requested as
+// soon as this tile's stage 1 is done, and a later tile of a strip requests only its flow
+// boxes. Returns false if a staging copy did not complete in time.
 template <typename T, bool NC, int R, int MODE, int TH, int CM>
 __device__ __forceinline__ bool lk_tile_step(const IterArgs &a, const StageMaps *maps, int tx0, int ty0, float2 ref,
-                                             float fp64_cond, float *smem, uint32_t &phase, bool carry_rt)
+                                             float fp64_cond, float *smem, uint32_t &phase, bool carry_rt,
+                                             const float2 *wrefs = nullptr, bool next = false)
 {
     const bool CARRY = CM == 2 ? carry_rt : CM == 1;
     using F = FixedTile<R, TH>;
@@ -1177,20 +1210,16 @@ __device__ __forceinline__ bool lk_tile_step(const IterArgs &a, const StageMaps 
     const int brow_end = box ? ((CARRY || ALL) ? F::RH : TH) : 0;
     int wx0 = 0, wy0 = 0;
     if (staged) {
-        constexpr int E = 16 / S;
-        const float2 wref = flow_mode<NC, MODE>(a, min(tx0 + LK_TW / 2, a.W - 1), min(ty0 + TH / 2, a.H - 1));
-        const int ox = __float2int_rn(fminf(fmaxf(wref.x, -(float)a.W), (float)a.W));
-        const int oy = __float2int_rn(fminf(fmaxf(wref.y, -(float)a.H), (float)a.H));
-        const int wx = tx0 - F::RE + ox - F::STAGE_MARGIN - 2;
-        wx0 = (wx >= 0 ? wx / E : -((-wx + E - 1) / E)) * E;   // a multiple of 16 bytes
-        wy0 = ty0 - R + oy - F::STAGE_MARGIN - 2;
+        // a later tile of a strip: its window was requested by the tile above
+        const bool early = OF_EARLY_WINDOW && CM == 2 && CARRY;
+        win_origin<R, TH, S>(a, tx0, ty0, CM == 2 ? wrefs[0] : win_ref<NC, MODE, TH>(a, tx0, ty0), wx0, wy0);
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, (uint32_t)(F::win_bytes(S) + nbox * F::FLOW_BOX_BYTES));
+            mbar_arrive_expect_tx(bar, (uint32_t)((early ? 0 : F::win_bytes(S)) + nbox * F::FLOW_BOX_BYTES));
             for (int b = 0; b < nbox; ++b)
                 tma_load_2d(P01 + (bx0 + b * F::FLOW_BH) * F::RWP2, &maps->flow, tx0 - F::RE,
                             ty0 - R + bx0 + b * F::FLOW_BH, bar);
-            tma_load_2d(win, &maps->i2, wx0, wy0, bar);
+            if (!early) tma_load_2d(win, &maps->i2, wx0, wy0, bar);
         }
 #if OF_PREFETCH_I1 == 1
         // while the boxes land: warm L2 with the region's rows of I1 (read by stage 1)
@@ -1269,6 +1298,17 @@ __device__ __forceinline__ bool lk_tile_step(const IterArgs &a, const StageMaps 
         }
     }
     __syncthreads();
+    if constexpr (CM == 2 && OF_EARLY_WINDOW) {
+        // the window is free: request the next tile's, which lands while this tile
+        // finishes (the barrier's next phase completes only on that tile's arrival)
+        if (staged && next && threadIdx.x == 0) {
+            int nx0, ny0;
+            win_origin<R, TH, S>(a, tx0, ty0 + TH, wrefs[1], nx0, ny0);
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, (uint32_t)F::win_bytes(S));
+            tma_load_2d(win, &maps->i2, nx0, ny0, bar);
+        }
+    }
     // P23's chunks start at warp 4, so that when the rows leave some warps an extra chunk
     // of P01 and of P4 (24 rows: 12 chunks and 384 items) the other warps take P23's
     box_h_pairs<R, TH>(P01, r0);
@@ -1331,9 +1371,15 @@ __device__ __forceinline__ bool lk_tile_fixed(const IterArgs &a, const StageMaps
     if constexpr (!MULTI) {   // one tile per unit (a.strip 1)
         return lk_tile_step<T, NC, R, MODE, TH, 0>(a, maps, tx0, t_first * TH, ref, fp64_cond, smem, phase, false);
     } else {
+        // the window estimates of the strip's tiles (strip_len: at most the 4 slots at
+        // OFF_WREF), loaded together before the first tile's staging
+        float2 *wrefs = reinterpret_cast<float2 *>(smem + F::OFF_WREF);
+        if (maps && a.stage_i2 && (int)threadIdx.x < t_end - t_first)
+            wrefs[threadIdx.x] = win_ref<NC, MODE, TH>(a, tx0, (t_first + (int)threadIdx.x) * TH);
 #pragma unroll 1
         for (int t = t_first; t < t_end; ++t)
-            if (!lk_tile_step<T, NC, R, MODE, TH, 2>(a, maps, tx0, t * TH, ref, fp64_cond, smem, phase, t > t_first))
+            if (!lk_tile_step<T, NC, R, MODE, TH, 2>(a, maps, tx0, t * TH, ref, fp64_cond, smem, phase, t > t_first,
+                                                     wrefs + (t - t_first), t + 1 < t_end))
                 return false;
         return true;
     }
