@@ -645,7 +645,7 @@ def extra_legs(args, torch, of, synth, src, I1, I2, us, vs, stream, plan16, flow
         of.compute_batch_host(flows, h1, h2, hu, hv, I1, I2, us, vs, stream=stream, chunk=0)
 
     Ke = max(3, args.steps // 2)
-    for key, fn, path in (("e2e", e2e_pipelined, "pinned host frames -> of_compute_batch_host (default chunks of 8 pairs, "
+    for key, fn, path in (("e2e", e2e_pipelined, "pinned host frames -> of_compute_batch_host (default chunks of about 8 Mpx, a quarter and a half of that at either end, "
                                                  "alternating between two compute streams; uploads and "
                                                  "downloads on two copy streams overlap the launches) -> pinned host u, v"),
                           ("e2e_unpipelined", e2e_serial, "pinned host frames -> of_compute_batch -> pinned host u, v, "

@@ -11,6 +11,11 @@
 
 using namespace of;
 
+// Level-0 megapixels of the default chunk of of_compute_batch_host.
+#ifndef OF_HOST_CHUNK_MPX
+#define OF_HOST_CHUNK_MPX 8.0
+#endif
+
 // ------------------------------------------------------ host-buffer pipelined form
 // of_compute_batch_host: the batch in chunks; chunk k's upload runs on a copy stream,
 // its launches after that upload on one of two compute streams (the caller's for even
@@ -95,17 +100,33 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
             return OF_EINVAL;
         if (!hI1s[i] && !hs[i]->has_prev) return OF_ESTATE;
     }
-    // default: chunks of about eight 1024^2 pairs, at most 24 chunks (measured on 64 such
+    // default: chunks of about eight 1024^2 pairs, at most 24 of them (measured on 64 such
     // pairs, fields/s for 3, 4, 6, 8, 11, 16, 22, 32 pairs per chunk: 9343, 9434, 9517, 9656,
-    // 9430, 9146, 8782, 7915; from 8 pairs on, a chunk's launches have the tiles for strips)
+    // 9430, 9146, 8782, 7915; from 8 pairs on, a chunk's launches have the tiles for strips),
+    // the first and the last two a quarter and a half of that, so that the pipeline fills
+    // (first upload) and drains (last launches and downloads) in less time
     int per = chunk;
+    std::vector<int> sizes;
     if (per <= 0) {
         double px = 0.0;
         for (int i = 0; i < n; ++i) px += (double)hs[i]->plan.H * hs[i]->plan.W;
-        per = (int)lround(8.0 * 1048576.0 / (px / n));
+        per = (int)lround(OF_HOST_CHUNK_MPX * 1048576.0 / (px / n));
         per = std::max(per, std::max(1, (n + 23) / 24));
+        const int q = std::max(1, per / 4), h = std::max(1, per / 2);
+        if (per >= 4 && n >= 2 * (q + h) + per) {
+            sizes = {q, h};
+            int rest = n - 2 * (q + h);
+            while (rest > 0) {
+                sizes.push_back(std::min(per, rest));
+                rest -= per;
+            }
+            sizes.push_back(h);
+            sizes.push_back(q);
+        }
     }
-    const int nch = (n + per - 1) / per;
+    if (sizes.empty())
+        for (int off = 0; off < n; off += per) sizes.push_back(std::min(per, n - off));
+    const int nch = (int)sizes.size();
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const PipeStreams *ps = pipe_streams();
     if (!ps) return OF_ECUDA;
@@ -131,9 +152,9 @@ extern "C" int of_compute_batch_host(int32_t n, const of_handle *hs, const void 
         return rc;
     };
     const size_t in_elem = hs[0]->plan.in_format == OF_U8 ? 1 : 2;
-    std::vector<const void *> d1(per);
-    for (int c = 0; c < nch; ++c) {
-        const int off = c * per, cnt = off + per <= n ? per : n - off;
+    std::vector<const void *> d1(*std::max_element(sizes.begin(), sizes.end()));
+    for (int c = 0, off = 0; c < nch; off += sizes[c], ++c) {
+        const int cnt = sizes[c];
         for (int i = off; i < off + cnt; ++i) {
             const size_t px = (size_t)hs[i]->plan.H * hs[i]->plan.W;
             if ((hI1s[i] && cudaMemcpyAsync(dI1s[i], hI1s[i], px * in_elem, cudaMemcpyHostToDevice, pp.up) != cudaSuccess) ||

@@ -269,7 +269,7 @@ def _host_ptr(t: torch.Tensor | None, dtype, p: Plan, name: str) -> int | None:
 def compute_batch_host(flows, hI1s, hI2s, hus, hvs, dI1s, dI2s, dus, dvs, stream=None, chunk=0):
     """of_compute_batch_host: frames from host tensors, fields into host tensors, the
     copies overlapped with the batched launches (chunks of `chunk` pairs, 0 = about
-    8 Mpx per chunk). hI1s[i] = None reuses the previous pyramid. Synchronise `stream` before
+    8 Mpx per chunk, smaller at either end of the batch). hI1s[i] = None reuses the previous pyramid. Synchronise `stream` before
     reading hus/hvs."""
     n = len(flows)
     img = [torch.uint8 if f.plan.in_format == OF_U8 else torch.uint16 for f in flows]

@@ -234,6 +234,36 @@ def test_host_buffer_pipeline_equals_device_batch(of, chunk, branches):
     of.tuning_clear()
 
 
+def test_host_pipeline_default_chunks_ramp(of):
+    # 24 pairs of 1024^2 with the default chunking: chunks of 2, 4, 8, 4, 4 and 2 pairs
+    # (smaller at either end of the batch) give the same bits as of_compute_batch
+    import torch
+    src = [synth.make_c2(1024, 1024, seed=50 + k) for k in range(4)]
+    n = 24
+    plan = of.Plan.make(1024, 1024, 3, 4, 3, bits=12, storage="f16")
+    fa = [of.Flow(plan) for _ in range(n)]
+    fb = [of.Flow(plan) for _ in range(n)]
+    pin = lambda a: torch.from_numpy(a.astype(np.int32)).to(torch.uint16).pin_memory()
+    h1 = [pin(src[i % 4].I1) for i in range(n)]
+    h2 = [pin(src[i % 4].I2) for i in range(n)]
+    dI1 = [torch.empty((1024, 1024), dtype=torch.uint16, device="cuda") for _ in range(n)]
+    dI2 = [torch.empty((1024, 1024), dtype=torch.uint16, device="cuda") for _ in range(n)]
+    hu = [torch.empty((1024, 1024), dtype=torch.float32).pin_memory() for _ in range(n)]
+    hv = [torch.empty((1024, 1024), dtype=torch.float32).pin_memory() for _ in range(n)]
+    du = [torch.empty((1024, 1024), dtype=torch.float32, device="cuda") for _ in range(n)]
+    dv = [torch.empty((1024, 1024), dtype=torch.float32, device="cuda") for _ in range(n)]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        of.compute_batch_host(fa, h1, h2, hu, hv, dI1, dI2, du, dv, stream=s, chunk=0)
+        ub, vb = of.compute_batch(fb, [to_dev(src[i % 4].I1) for i in range(n)],
+                                  [to_dev(src[i % 4].I2) for i in range(n)], stream=s)
+    s.synchronize()
+    for i in range(n):
+        assert torch.equal(hu[i], ub[i].cpu()) and torch.equal(hv[i], vb[i].cpu()), i
+    for f in fa + fb:
+        f.close()
+
+
 def test_more_pairs_than_one_phase_launch_holds(of):
     # 70 small pairs: each phase is split into launches of at most 64 pairs; every
     # field equals of_compute's, including pairs that reuse their previous pyramid
