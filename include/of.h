@@ -154,8 +154,9 @@ int of_compute_batch(int32_t n, const of_handle *hs, const void *const *I1s, con
  * of_compute_batch from and to HOST buffers, with the copies overlapped with the
  * computation. The pairs are taken in chunks of `chunk` pairs (0: about 8 Mpx of level 0
  * per chunk, i.e. eight 1024^2 pairs, at most 24 such chunks, with the first and the last
- * a quarter and the second and the second-to-last half of that when the batch holds at
- * least three chunks' worth, so that the pipeline fills and drains faster): chunk
+ * a quarter and the second and the second-to-last half of that when such a chunk holds at
+ * least 4 pairs and the batch at least 2.5 chunks' worth, so that the pipeline fills and
+ * drains faster): chunk
  * k's frames are uploaded (hI1s/hI2s -> dI1s/dI2s) on an internal stream, its
  * batched launch runs after that upload (even chunks on `stream`, odd chunks on a
  * compute stream the library keeps for the calling thread and device until the thread
